@@ -1,0 +1,97 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and by the oracle.
+
+This module only draws random inputs (tensors, initial vectors); it holds none of the
+sketching or power-method arithmetic.  Every generator takes an explicit integer seed
+and uses numpy's PCG64 stream, so both sides of a parity test see identical bytes.
+
+Workload shapes follow the paper's synthetic experiment (Sec. 5.1): a symmetric tensor
+built from an orthonormal set of components plus a symmetric Gaussian noise tensor
+whose independent entries are those with i <= j <= k.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "rng",
+    "orthonormal_columns",
+    "planted_symmetric",
+    "symmetric_noise",
+    "gaussian_inits",
+    "random_symmetric",
+    "random_symmetric_int",
+    "random_vector",
+]
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+def orthonormal_columns(n: int, k: int, seed: int) -> np.ndarray:
+    """n x k matrix with orthonormal columns (QR of a Gaussian matrix, sign-fixed)."""
+    g = rng(seed).standard_normal((n, k))
+    q, r = np.linalg.qr(g)
+    q = q * np.sign(np.diag(r))[None, :]
+    return q
+
+
+def symmetric_noise(n: int, std: float, seed: int, dtype=np.float64) -> np.ndarray:
+    """Symmetric n^3 tensor: entry (i,j,k) copies an N(0, std^2) draw made for the
+    sorted triple (min, mid, max) -- one independent draw per i <= j <= k."""
+    out = np.empty((n, n, n), dtype=dtype)
+    if std == 0.0 or n == 0:
+        out[...] = 0
+        return out
+    g = rng(seed).standard_normal((n, n, n)) * std
+    jj, kk = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    for i in range(n):
+        ii = np.full_like(jj, i)
+        lo = np.minimum(np.minimum(ii, jj), kk)
+        hi = np.maximum(np.maximum(ii, jj), kk)
+        mid = ii + jj + kk - lo - hi
+        out[i] = g[lo, mid, hi]
+    return out
+
+
+def planted_symmetric(n: int, k: int, noise: float, seed: int,
+                      lam_low: float = 1.0, lam_high: float = 2.0,
+                      dtype=np.float64):
+    """T = sum_r lam_r a_r (x) a_r (x) a_r + E with orthonormal a_r, lam_r ~ U[lam_low, lam_high]
+    and E from :func:`symmetric_noise`.  Returns (T, lam, A) with A of shape n x k."""
+    r = rng(seed)
+    lam = r.uniform(lam_low, lam_high, size=k)
+    A = orthonormal_columns(n, k, seed + 1)
+    T = symmetric_noise(n, noise, seed + 2, dtype=np.float64)
+    for i in range(n):
+        T[i] += (A * (lam * A[i])[None, :]) @ A.T
+    return T.astype(dtype, copy=False), lam, A
+
+
+def random_symmetric(n: int, seed: int, dtype=np.float64) -> np.ndarray:
+    """Dense symmetric tensor with N(0,1) independent entries (i <= j <= k)."""
+    return symmetric_noise(n, 1.0, seed, dtype=dtype)
+
+
+def random_symmetric_int(n: int, seed: int, low: int = -1000, high: int = 1000) -> np.ndarray:
+    """Dense symmetric int32 tensor with independent integer entries for i <= j <= k."""
+    g = rng(seed).integers(low, high + 1, size=(n, n, n), dtype=np.int64)
+    out = np.empty((n, n, n), dtype=np.int32)
+    jj, kk = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    for i in range(n):
+        ii = np.full_like(jj, i)
+        lo = np.minimum(np.minimum(ii, jj), kk)
+        hi = np.maximum(np.maximum(ii, jj), kk)
+        mid = ii + jj + kk - lo - hi
+        out[i] = g[lo, mid, hi]
+    return out
+
+
+def gaussian_inits(k: int, L: int, n: int, seed: int) -> np.ndarray:
+    """k x L x n standard Gaussian draws; normalising each row gives a uniform point on the
+    unit sphere (the initial vectors of the robust tensor power method, Alg. 1)."""
+    return rng(seed).standard_normal((k, L, n))
+
+
+def random_vector(n: int, seed: int) -> np.ndarray:
+    return rng(seed).standard_normal(n)
