@@ -1,0 +1,358 @@
+"""Benchmark: sketched robust tensor power method on one GB300 (per replica).
+
+Workload (default): dense symmetric FP32 tensor, n = 400 (256 MB), 20 planted orthonormal
+components with lambda ~ U[1, 2] plus symmetric Gaussian noise (std 0.005); B = 10 colliding
+sketches of length b = 2^14; Alg. 1 with L = 50 initial vectors, T = 30 power updates and
+k = 20 deflation rounds.  One step = hashes + sketch build + Alg. 1 (all k rounds).
+
+value = T^(I,u,u) evaluations per second (each against all B sketches, then the median), summed
+over replicas.  The JSON line also carries the sketch-build bandwidth against HBM, the roofline
+of the dominant kernel, an end-to-end figure through the public call with host buffers, the
+oracle timed on the host cores, SM clocks sampled during the timed region and the number of
+kernel launches.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "sketched T(I,u,u) contractions/s + sketch-build GB/s vs HBM roofline, 1 GB300"
+UNIT = "contractions/s"
+CFG = dict(n=400, k=20, noise=0.005, B=10, log2b=14, L=50, T=30, seed=1)
+WORKLOAD = ("dense symmetric FP32 n=400 (256 MB), k=20 planted orthonormal, lambda~U[1,2], "
+            "noise 0.005; B=10, b=2^14, L=50, T=30, full sketch build + power method + deflation")
+
+# FP32 lanes per SM on GB300 and its SM count / maximum SM clock (used for the ALU roof)
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+SMEM_BYTES_PER_CLK = 128
+
+
+def fft_flops(logn: int) -> float:
+    """5 N log2 N real flops per complex N-point DFT (the usual FFT flop count)."""
+    return 5.0 * (1 << logn) * logn
+
+
+def contraction_flops(log2b: int) -> float:
+    """Algorithmic flops of one sketch-contraction T^(m)(I,u,u) as the kernel organises it:
+    forward and inverse length-b DFTs plus forward and inverse length-b/2 DFTs, plus the
+    spectral products (3 complex multiply-adds per frequency of b)."""
+    return 2 * fft_flops(log2b) + 2 * fft_flops(log2b - 1) + 3 * 8.0 * (1 << log2b)
+
+
+def contraction_smem_bytes(log2b: int) -> float:
+    """Shared-memory bytes moved by one sketch-contraction: every Stockham pass reads and writes
+    its buffer once (radix-16 passes for length b, radix-8 passes for length b/2)."""
+    b = 1 << log2b
+    passes_b = math.ceil(log2b / 4)
+    passes_h = math.ceil((log2b - 1) / 3)
+    return 2 * (passes_b * 2 * 8 * b + passes_h * 2 * 8 * (b // 2)) + 4 * 8 * b
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ inputs
+def make_inputs(cfg):
+    import synth
+    T, lam, A = synth.planted_symmetric(cfg["n"], cfg["k"], cfg["noise"], cfg["seed"], dtype=np.float32)
+    U0 = synth.gaussian_inits(cfg["k"], cfg["L"], cfg["n"], cfg["seed"] + 1).astype(np.float32)
+    return T, U0
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def oracle_contraction_rate(cfg, budget_s: float, max_vectors: int | None = None):
+    """Time the oracle's T^(I,u,u) (FFT engine, all B sketches + median) on the host; returns
+    (contractions/s, vectors done, seconds)."""
+    import oracle as O
+    b = 1 << cfg["log2b"]
+    n, B = cfg["n"], cfg["B"]
+    h, g = O.cs_hashes(cfg["seed"], B, cfg["log2b"], [n])
+    # the cost of a contraction does not depend on the sketch values, so the timed sample
+    # contracts against random sketches instead of paying for the oracle's O(n^3 B) build
+    r = np.random.default_rng(0)
+    S = r.standard_normal((B, b)) + 1j * r.standard_normal((B, b))
+    U = r.standard_normal((cfg["L"], n))
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        O.power_step_sketched(S, U[done % cfg["L"]], h[:, 0], g[:, 0], b, "fft")
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_vectors and done >= max_vectors):
+            return done / el, done, el
+
+
+def run_reference(args):
+    """The oracle as it stands, on the host cores: each step is one power update of a bounded
+    sample of the L initial vectors against all B sketches."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg = dict(CFG)
+    per_step = 4
+    times = []
+    for s in range(args.warmup + args.steps):
+        rate, done, el = oracle_contraction_rate(cfg, budget_s=1e9, max_vectors=per_step)
+        if s >= args.warmup:
+            times.append(el)
+    tot = sum(times)
+    value = per_step * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{per_step} of the L=50 vectors per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} T^(I,u,u) evaluations (B=10 sketches each, "
+                                       "numpy FP64 FFT engine, random sketch values) per step",
+                             "host_cpus": os.cpu_count()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1506_04448_gb300 as tsk
+
+    cfg = dict(CFG)
+    n, k, B, log2b, L, T_it = cfg["n"], cfg["k"], cfg["B"], cfg["log2b"], cfg["L"], cfg["T"]
+    b = 1 << log2b
+    T_host, U0_host = make_inputs(cfg)
+    T_d = torch.from_numpy(T_host).to(dev)
+    U0_d = torch.from_numpy(U0_host).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        h, g = tsk.cs_hashes(cfg["seed"], B, log2b, [n], dev)
+        S = tsk.sketch_tensor(T_d, h, g, log2b)
+        return tsk.robust_power_method(S, h, g, U0_d, T_it)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    tsk.check_status(dev)
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            res = step()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    t_ms = ev0.elapsed_time(ev1)
+    clocks = clk.summary()
+    tsk.check_status(dev)
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = tt.item()
+    per_step_ms = t_ms / args.steps
+    contractions = k * L * T_it
+    value = world * contractions * args.steps / (t_ms / 1e3)
+
+    # dominant kernel: the fused contraction kernel in its power-step launch shape (B x L blocks)
+    h, g = tsk.cs_hashes(cfg["seed"], B, log2b, [n], dev)
+    S = tsk.sketch_tensor(T_d, h, g, log2b)
+    FS = tsk.sketch_fft(S)
+    U = torch.nn.functional.normalize(U0_d[0], dim=1).contiguous()
+    for _ in range(3):
+        tsk.contract_iuu(FS, S, h, g, U)
+    reps = 50
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        tsk.contract_iuu(FS, S, h, g, U)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    k_ms = e0.elapsed_time(e1) / reps
+    flops = B * L * contraction_flops(log2b)
+    clock_mhz = SM_MAX_MHZ
+    alu_peak = SMS * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
+    smem_peak = SMS * SMEM_BYTES_PER_CLK * clock_mhz * 1e6 / 1e9
+    achieved_tf = flops / (k_ms / 1e3) / 1e12
+    smem_gbs = B * L * contraction_smem_bytes(log2b) / (k_ms / 1e3) / 1e9
+
+    # sketch build: wedge entries read once (4 B each) + hash tables
+    pk, pk_kind = peaks()
+    W = n * (n + 1) * (n + 2) // 6
+    build_bytes = 4 * W + B * n * 5 + B * b * 8
+    for _ in range(3):
+        tsk.sketch_tensor(T_d, h, g, log2b)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    bt = []
+    for _ in range(10):
+        flush.fill_(1.0)   # evict the tensor from L2 between launches
+        e0.record(stream)
+        tsk.sketch_tensor(T_d, h, g, log2b)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        bt.append(e0.elapsed_time(e1))
+    b_ms = statistics.median(bt)
+    build_gbs = build_bytes / (b_ms / 1e3) / 1e9
+
+    # end to end through the public call with pinned host buffers
+    T_pin = torch.from_numpy(T_host).pin_memory()
+    U0_pin = torch.from_numpy(U0_host).pin_memory()
+    tsk.decompose_symmetric(T_pin, k, L, T_it, B, log2b, cfg["seed"], U0_pin, dev)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        out = tsk.decompose_symmetric(T_pin, k, L, T_it, B, log2b, cfg["seed"], U0_pin, dev)
+    torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    d2h = sum(v.numel() * v.element_size() for v in out.values())
+    h2d = T_pin.numel() * 4 + U0_pin.numel() * 4
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, done, el = oracle_contraction_rate(cfg, budget_s=args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{done} T^(I,u,u) evaluations against B=10 sketches (b=2^14, numpy FP64 "
+                         f"FFT engine, random sketch values) in {el:.1f} s",
+               "host_cpus": os.cpu_count()}
+
+    launches_per_step = 3 + k * (T_it + 2)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": per_step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "k": k, "B": B, "b": b, "L": L, "T": T_it,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (T is 256 MB); sketch build timed after an L2 flush"},
+        "sketch_contractions_per_s": value * B,
+        "roofline": {"kernel": "contract_kernel<14, MODE_IUU> (grid B x L = 10 x 50)",
+                     "bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tf / alu_peak, "traffic": None,
+                     "launch_ms": k_ms, "flops_per_launch": flops,
+                     "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {clock_mhz:.0f} MHz",
+                     "smem": {"achieved": smem_gbs, "peak": smem_peak, "unit": "GB/s",
+                              "frac": smem_gbs / smem_peak}},
+        "sketch_build": {"bound": "hbm", "achieved": build_gbs, "peak": pk["hbm_gbs"],
+                         "unit": "GB/s", "frac": build_gbs / pk["hbm_gbs"], "launch_ms": b_ms,
+                         "bytes": build_bytes, "peak_kind": pk_kind},
+        "e2e": {"value": contractions / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "s_per_step": e2e_s},
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "gpu_launches": launches_per_step * args.steps,
+        "results": {"lambda_head": [round(float(x), 6) for x in res["lam"][:5].cpu()]},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * tsk.h -- C ABI of the GB300 (sm_103a) tensor-sketch library.
+ *
+ * Implements the hot path of the sketched robust tensor power method of Wang, Tung, Smola and
+ * Anandkumar, "Fast and Guaranteed Tensor Decomposition via Sketching" (NIPS 2015):
+ * colliding count sketches of symmetric tensors (Sec. 3.3), rank-1 sketches by FFT (Eq. 4),
+ * the sketched contractions T^(I,u,u) and T^(u,u,u) read from inverse FFTs at hashed
+ * positions (Prop. 1, App. B), the median over B sketches and deflation (Alg. 1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers are DEVICE pointers owned by the caller unless the argument says "host".
+ *   The library never frees or retains caller memory.
+ * - Every call is asynchronous on the stream bound to the context (tsk_ctx_set_stream);
+ *   results are valid once that stream has been synchronised.
+ * - Argument errors are detected on the host before anything is enqueued: the call returns
+ *   TSK_EINVAL (or TSK_EUNSUPPORTED for a valid but unimplemented size) and enqueues nothing.
+ * - Errors found on the device (a zero or non-finite norm in a power update) are recorded
+ *   in a status word of the context; tsk_ctx_status() synchronises and returns/clears it.
+ * - A launch or allocation failure of the CUDA runtime returns TSK_ECUDA / TSK_ENOMEM.
+ * - The only memory the library allocates is the context's scratch workspace (grown on
+ *   demand, freed by tsk_ctx_destroy).
+ * - b = 2^log2b is the sketch length.  Sketches are stored as [B][b] arrays of
+ *   interleaved complex numbers (re, im).  DFTs are unnormalised forward
+ *   F(x)_f = sum_t x_t exp(-2 pi i f t / b); inverse transforms carry 1/b.
+ * - Hash tables: h int32 [B][M][nmax] with values in [0, b); g uint8 [B][M][nmax] with values
+ *   in {0,1,2,3}.  M = 1 (colliding, symmetric sketch) or M = 3 (asymmetric sketch).  The
+ *   complex sign is sigma(i) = sqrt(-1)^g(i) (Sec. 3.3, m = 4); the real sign of the
+ *   asymmetric sketch is xi(i) = 1 - 2 (g(i) & 1) (Eq. 1).
+ */
+#ifndef TSK_H_
+#define TSK_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tsk_ctx tsk_ctx;
+
+enum tsk_status {
+  TSK_OK = 0,
+  TSK_EINVAL = -1,        /* bad argument (null pointer, size out of range, bad dtype) */
+  TSK_ENOMEM = -2,        /* workspace allocation failed */
+  TSK_ECUDA = -3,         /* CUDA runtime error (launch, copy, device query) */
+  TSK_ETIMEOUT = -4,      /* reserved: a bounded device-side wait gave up */
+  TSK_ENONFINITE = -5,    /* power update met ||v_bar|| = 0 or a non-finite norm */
+  TSK_EUNSUPPORTED = -6   /* valid request outside the implemented sizes */
+};
+
+enum tsk_dtype {
+  TSK_F32 = 0,   /* float */
+  TSK_F64 = 1,   /* double */
+  TSK_I32 = 2,   /* int32 */
+  TSK_C64 = 3,   /* complex float, interleaved (re, im) */
+  TSK_C128 = 4,  /* complex double, interleaved */
+  TSK_CI64 = 5   /* complex int64, interleaved: exact integer sketches */
+};
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` bound to `stream` (a cudaStream_t; NULL = legacy
+ * default stream).  *out receives the handle.  Returns TSK_OK or TSK_ECUDA/TSK_EINVAL. */
+int tsk_ctx_create(int device, void* stream, tsk_ctx** out);
+
+/* Free the context's workspace and the context itself.  Synchronises its stream first. */
+int tsk_ctx_destroy(tsk_ctx* ctx);
+
+/* Re-bind the context to another stream of the same device (cheap; no synchronisation). */
+int tsk_ctx_set_stream(tsk_ctx* ctx, void* stream);
+
+/* Synchronise the context's stream, then return and clear the first device-side error
+ * recorded since the last call (TSK_OK if none). */
+int tsk_ctx_status(tsk_ctx* ctx);
+
+/* Static, human-readable text for a status code. */
+const char* tsk_strerror(int status);
+
+/* ---------------------------------------------------------------- hashing (Sec. 2, Sec. 3.3, Prop. 2) */
+
+/* Draw the hash tables of B independent sketches.  For sketch m and mode j (j < M):
+ *   h[m][j][i] = ((a_0 + a_1 i + ... + a_5 i^5) mod P) mod b      (6-wise independent, Prop. 2)
+ *   g[m][j][i] = ((c_0 + c_1 i + ... + c_11 i^11) mod P) mod 4    (12-wise independent)
+ * with P = 2^61 - 1 and coefficient e of table w (0 = h, 1 = g) equal to output number
+ * ((m*M + j)*2 + w)*16 + e of the SplitMix64 stream started at `seed`, reduced mod P.
+ * dims_host: host array of M mode sizes; nmax = max(dims_host).  Entries i >= dims[j] are
+ * written as 0.  Requires 1 <= B, M in {1,3}, 1 <= log2b <= 24, 0 <= dims[j] < 2^31. */
+int cs_hashes(tsk_ctx* ctx, uint64_t seed, int B, int log2b, int M, const int64_t* dims_host,
+              int32_t* h, uint8_t* g);
+
+/* ---------------------------------------------------------------- sketch construction (Eq. 1, Eq. 7) */
+
+/* Tensor sketches of a dense row-major tensor T.
+ * M = 1: colliding sketch of a SYMMETRIC n x n x n tensor (Eq. 7):
+ *     S[m][t] = sum over ordered (i,j,k) with (h(i)+h(j)+h(k)) mod b = t of sigma_i sigma_j sigma_k T_ijk,
+ *   computed from the entries with i <= j <= k only, each weighted by kappa in {1,3,6}
+ *   (Sec. 3.3: all permutations of an entry collide); T must be symmetric.
+ * M = 3: asymmetric sketch of an n1 x n2 x n3 tensor (Eq. 1), real-valued, stored with
+ *   zero imaginary part: S[m][t] = sum_{(h1+h2+h3) mod b = t} xi1 xi2 xi3 T_ijk.
+ * in_dtype: TSK_F32 | TSK_F64 | TSK_I32.  acc_dtype: TSK_C64 (float accumulation, any input),
+ *   TSK_C128 (double accumulation, F64 input) or TSK_CI64 (exact int64, I32 input).
+ * S: [B][b] of acc_dtype.  accumulate = 0 overwrites S, 1 adds to it.
+ * Limits: symmetric path log2b <= 14 (M = 1), n <= 8192. */
+int sketch_tensor(tsk_ctx* ctx, const void* T, int in_dtype, int M, const int64_t* dims_host,
+                  const int32_t* h, const uint8_t* g, int B, int log2b,
+                  void* S, int acc_dtype, int accumulate);
+
+/* Batched length-b DFT of B complex float vectors (S_in, S_out: [B][b] TSK_C64; may alias).
+ * inverse = 0: unnormalised forward transform; 1: inverse transform including 1/b. */
+int sketch_fft(tsk_ctx* ctx, const float* S_in, float* S_out, int B, int log2b, int inverse);
+
+/* Rank-1 sketches by FFT (Eq. 4, Sec. 3.1 linearity).  For every sketch m:
+ *   M = 1 (colliding):  S[m] (+)= sum_c w[c] * (s~_{u_c} * s~_{u_c} * s~_{u_c})
+ *   M = 3 (asymmetric): S[m] (+)= sum_c w[c] * (s_{1,u_c} * s_{2,v_c} * s_{3,w_c})
+ * computed as F^{-1}(sum_c w_c F(s_1) o F(s_2) o F(s_3)).
+ * w: [count] float; U: [count][n1], V: [count][n2], W: [count][n3] float (V, W only for M = 3);
+ * dims_host: M mode sizes.  domain = 0 writes the time-domain sketch, 1 its DFT.
+ * S: [B][b] TSK_C64; accumulate = 0 overwrites, 1 adds.  Uses count*B FFTs.
+ * Limits: log2b in [8, 14]. */
+int sketch_rank1(tsk_ctx* ctx, int64_t count, const float* w, const float* U, const float* V,
+                 const float* W, int M, const int64_t* dims_host, const int32_t* h,
+                 const uint8_t* g, int B, int log2b, int domain, float* S, int accumulate);
+
+/* ---------------------------------------------------------------- contractions (Prop. 1, App. B) */
+
+/* Sketched T^(I,u,u) for L vectors against B colliding sketches (M = 1).  For sketch m and
+ * vector u = U[l] (used as given):
+ *   v_i^(m) = Re[ 1/6 conj(sigma_i) (g_2 + g_1)[h_i] + 1/3 conj(sigma_i)^2 u_i g_0[2 h_i mod b]
+ *               + 1/3 conj(sigma_i)^3 u_i^2 S[3 h_i mod b] ]
+ * where g_0 = F^-1(FS o conj F s~_u), g_1 = F^-1(FS o conj F s~_{2,u o u}),
+ *       g_2 = F^-1(FS o conj(F s~_u)^2)  (App. B, Eq. 14 with coefficients 1/3,1/6,1/6,1/3
+ *       -- the printed 1 and 1 on the outer terms give a biased estimate).
+ * FS: [B][b] TSK_C64 = DFT of S; S: [B][b] TSK_C64 time-domain sketch; U: [L][n] float.
+ * Vmed: [L][n] float, median over m of v^(m) (mean of the two middle values for even B).
+ * Vall: optional [L][B][n] float, every v^(m) (NULL: kept in workspace only).
+ * Limits: log2b in [8, 14], 1 <= B <= 64, 1 <= n <= 8192. */
+int contract_iuu(tsk_ctx* ctx, const float* FS, const float* S, const int32_t* h,
+                 const uint8_t* g, int B, int log2b, const float* U, int L, int64_t n,
+                 float* Vmed, float* Vall);
+
+/* Sketched T^(u,u,u) (App. B, Eq. 13, all terms as time-domain inner products):
+ *   lambda^(m) = Re[ 1/6 <S, s~_u * s~_u * s~_u> + 1/2 <S, s~_{2,u o u} * s~_u> + 1/3 <S, s~_{3,u o u o u}> ]
+ * evaluated as (1/b) sum_f FS[f] conj(U_f^3/6 + V_f U_f/2) plus the sparse third term.
+ * lam_med: [L] float, median over the B sketches; lam_all: optional [L][B] float.
+ * Same limits as contract_iuu. */
+int contract_uuu(tsk_ctx* ctx, const float* FS, const float* S, const int32_t* h,
+                 const uint8_t* g, int B, int log2b, const float* U, int L, int64_t n,
+                 float* lam_med, float* lam_all);
+
+/* ---------------------------------------------------------------- Alg. 1 */
+
+/* Fast robust tensor power method (Alg. 1) on B colliding sketches of a symmetric tensor.
+ * S: [B][b] TSK_C64 time-domain sketches (read only).  U0: [k][L][n] float initial vectors of
+ * every deflation round (normalised on the device before use).  For r = 0..k-1:
+ *   T power updates u <- median_m T^(m)(I,u,u) / ||.|| for all L vectors;
+ *   lambda_tau = median_m T^(m)(u,u,u); tau* = first argmax; (lambda^, u^) = (lambda_tau*, u_tau*);
+ *   deflation: every sketch loses lambda^ * s~_{u^ (x) u^ (x) u^}.
+ * Outputs: lambda [k] double, Vout [k][n] float, tau_star [k] int32 (may be NULL),
+ * S_deflated: optional [B][b] TSK_C64 receiving the sketches after the k-th deflation.
+ * A zero/non-finite norm in an update is reported by tsk_ctx_status() as TSK_ENONFINITE.
+ * Limits: as contract_iuu, 1 <= L <= 4096, T >= 1, k >= 0. */
+int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* h, const uint8_t* g,
+                        int B, int log2b, int64_t n, int k, int L, int T, const float* U0,
+                        double* lambda, float* Vout, int32_t* tau_star, float* S_deflated);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSK_H_ */

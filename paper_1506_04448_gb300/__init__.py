@@ -1,0 +1,11 @@
+"""GB300 (sm_103a) implementation of the sketched robust tensor power method of
+Wang, Tung, Smola & Anandkumar, "Fast and Guaranteed Tensor Decomposition via Sketching".
+
+The compute path lives in libtsk.so (csrc/*.cu, C ABI in include/tsk.h); this package is its
+thin binding.  Entry points: cs_hashes, sketch_tensor, sketch_fft, sketch_rank1, contract_iuu,
+contract_uuu, robust_power_method, decompose_symmetric.
+"""
+from .api import (cs_hashes, sketch_tensor, sketch_fft, sketch_rank1,  # noqa: F401
+                  contract_iuu, contract_uuu, robust_power_method, decompose_symmetric,
+                  ctx_status, check_status)
+from ._lib import TskError, LIB_PATH, load as load_library  # noqa: F401

@@ -1,0 +1,280 @@
+"""Python binding of the C ABI in include/tsk.h: argument marshalling only.
+
+Every function takes CUDA torch tensors, checks shapes and dtypes, allocates outputs with torch
+(device memory is the only thing torch provides here) and calls the library on the current
+torch stream of the tensors' device.  All arithmetic happens in libtsk.so.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import torch
+
+from . import _lib
+
+_ctx_lock = threading.Lock()
+_ctxs: dict[int, int] = {}
+
+
+def _ctx(device: torch.device) -> int:
+    """Per-device library context bound to the device's current torch stream."""
+    lib = _lib.load()
+    idx = device.index if device.index is not None else torch.cuda.current_device()
+    with _ctx_lock:
+        c = _ctxs.get(idx)
+        if c is None:
+            h = ctypes.c_void_p()
+            with torch.cuda.device(idx):
+                _lib.check("tsk_ctx_create", lib.tsk_ctx_create(idx, None, ctypes.byref(h)))
+            c = h.value
+            _ctxs[idx] = c
+    stream = torch.cuda.current_stream(idx).cuda_stream
+    _lib.check("tsk_ctx_set_stream", lib.tsk_ctx_set_stream(c, ctypes.c_void_p(stream)))
+    return c
+
+
+def _ptr(t: torch.Tensor | None) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _need(t: torch.Tensor, name: str, dtype, device: torch.device, shape=None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.device.type != "cuda" or t.device != device:
+        raise ValueError(f"{name} must live on {device}, got {t.device}")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _dims(dims) -> ctypes.Array:
+    arr = (ctypes.c_int64 * len(dims))(*[int(d) for d in dims])
+    return arr
+
+
+def _hashes_shape(h: torch.Tensor, g: torch.Tensor):
+    if h.dim() == 2:
+        h = h.unsqueeze(1)
+        g = g.unsqueeze(1)
+    if h.dim() != 3 or h.shape != g.shape:
+        raise ValueError("h and g must have shape [B][M][nmax] (or [B][n] for M = 1)")
+    return h, g
+
+
+def ctx_status(device: torch.device | str | int = "cuda") -> int:
+    """Synchronise and return/clear the first device-side status code (0 = ok)."""
+    if isinstance(device, int):
+        device = torch.device("cuda", device)
+    device = torch.device(device) if not isinstance(device, torch.device) else device
+    return _lib.load().tsk_ctx_status(_ctx(device))
+
+
+def check_status(device: torch.device | str = "cuda") -> None:
+    rc = ctx_status(device)
+    _lib.check("device status", rc)
+
+
+# ------------------------------------------------------------------ hashing
+def cs_hashes(seed: int, B: int, log2b: int, dims, device="cuda"):
+    """Hash tables of B sketches: (h int32 [B][M][nmax], g uint8 [B][M][nmax])."""
+    device = torch.device(device)
+    dims = [int(d) for d in dims]
+    M = len(dims)
+    nmax = max(dims) if dims else 0
+    h = torch.empty((B, M, nmax), dtype=torch.int32, device=device)
+    g = torch.empty((B, M, nmax), dtype=torch.uint8, device=device)
+    rc = _lib.load().cs_hashes(_ctx(device), ctypes.c_uint64(seed & (2**64 - 1)), B, log2b, M,
+                               _dims(dims), _ptr(h), _ptr(g))
+    _lib.check("cs_hashes", rc)
+    return h, g
+
+
+# ------------------------------------------------------------------ sketches
+_IN_DTYPES = {torch.float32: _lib.TSK_F32, torch.float64: _lib.TSK_F64, torch.int32: _lib.TSK_I32}
+
+
+def sketch_tensor(T: torch.Tensor, h: torch.Tensor, g: torch.Tensor, log2b: int, *,
+                  S: torch.Tensor | None = None, accumulate: bool = False, acc: str = "c64"):
+    """Tensor sketches of a dense tensor.  h.shape[1] == 1: colliding sketch of a symmetric
+    n^3 tensor (Eq. 7); 3: asymmetric sketch (Eq. 1).  acc: 'c64' (complex64 [B][b]),
+    'c128' (complex128 [B][b]) or 'ci64' (int64 [B][b][2], exact)."""
+    device = T.device
+    if T.dtype not in _IN_DTYPES:
+        raise TypeError("T must be float32, float64 or int32")
+    _need(T, "T", T.dtype, device)
+    h, g = _hashes_shape(h, g)
+    _need(h, "h", torch.int32, device)
+    _need(g, "g", torch.uint8, device)
+    B, M, nmax = h.shape
+    if T.dim() != 3:
+        raise ValueError("T must be 3-dimensional")
+    if M == 1 and not (T.shape[0] == T.shape[1] == T.shape[2] == nmax):
+        raise ValueError("symmetric sketch needs an n x n x n tensor with n = h.shape[-1]")
+    if M == 3 and max(T.shape) != nmax:
+        raise ValueError("asymmetric sketch needs max(T.shape) == h.shape[-1]")
+    b = 1 << log2b
+    if acc == "c64":
+        shape, dt, code = (B, b), torch.complex64, _lib.TSK_C64
+    elif acc == "c128":
+        shape, dt, code = (B, b), torch.complex128, _lib.TSK_C128
+    elif acc == "ci64":
+        shape, dt, code = (B, b, 2), torch.int64, _lib.TSK_CI64
+    else:
+        raise ValueError("acc must be 'c64', 'c128' or 'ci64'")
+    if S is None:
+        if accumulate:
+            raise ValueError("accumulate=True needs S")
+        S = torch.empty(shape, dtype=dt, device=device)
+    _need(S, "S", dt, device, shape)
+    dims = list(T.shape) if M == 3 else [T.shape[0]]
+    rc = _lib.load().sketch_tensor(_ctx(device), _ptr(T), _IN_DTYPES[T.dtype], M, _dims(dims),
+                                   _ptr(h), _ptr(g), B, log2b, _ptr(S), code, int(accumulate))
+    _lib.check("sketch_tensor", rc)
+    return S
+
+
+def sketch_fft(S: torch.Tensor, inverse: bool = False, out: torch.Tensor | None = None):
+    """Batched DFT of the rows of a complex64 [B][b] tensor (inverse includes 1/b)."""
+    device = S.device
+    _need(S, "S", torch.complex64, device)
+    B, b = S.shape
+    log2b = b.bit_length() - 1
+    if 1 << log2b != b:
+        raise ValueError("sketch length must be a power of two")
+    out = torch.empty_like(S) if out is None else _need(out, "out", torch.complex64, device, S.shape)
+    rc = _lib.load().sketch_fft(_ctx(device), _ptr(S), _ptr(out), B, log2b, int(bool(inverse)))
+    _lib.check("sketch_fft", rc)
+    return out
+
+
+def sketch_rank1(w: torch.Tensor, U: torch.Tensor, h: torch.Tensor, g: torch.Tensor, log2b: int, *,
+                 V: torch.Tensor | None = None, W: torch.Tensor | None = None,
+                 domain: str = "time", S: torch.Tensor | None = None, accumulate: bool = False):
+    """S (+)= sum_c w[c] sketch(U[c] (x) V[c] (x) W[c]) (Eq. 4); V = W = None with M = 1
+    gives the colliding sketch of U[c]^(x)3."""
+    device = U.device
+    h, g = _hashes_shape(h, g)
+    _need(h, "h", torch.int32, device)
+    _need(g, "g", torch.uint8, device)
+    B, M, nmax = h.shape
+    count = U.shape[0]
+    _need(w, "w", torch.float32, device, (count,))
+    _need(U, "U", torch.float32, device)
+    dims = [U.shape[1]]
+    if M == 3:
+        if V is None or W is None:
+            raise ValueError("asymmetric rank-1 sketches need V and W")
+        _need(V, "V", torch.float32, device)
+        _need(W, "W", torch.float32, device)
+        dims = [U.shape[1], V.shape[1], W.shape[1]]
+    b = 1 << log2b
+    if S is None:
+        if accumulate:
+            raise ValueError("accumulate=True needs S")
+        S = torch.empty((B, b), dtype=torch.complex64, device=device)
+    _need(S, "S", torch.complex64, device, (B, b))
+    dom = {"time": 0, "freq": 1}[domain]
+    rc = _lib.load().sketch_rank1(_ctx(device), count, _ptr(w), _ptr(U), _ptr(V), _ptr(W), M,
+                                  _dims(dims), _ptr(h), _ptr(g), B, log2b, dom, _ptr(S),
+                                  int(accumulate))
+    _lib.check("sketch_rank1", rc)
+    return S
+
+
+# ------------------------------------------------------------------ contractions
+def _contract_common(FS, S, h, g, U):
+    device = U.device
+    _need(FS, "FS", torch.complex64, device)
+    B, b = FS.shape
+    _need(S, "S", torch.complex64, device, (B, b))
+    h, g = _hashes_shape(h, g)
+    if h.shape[1] != 1:
+        raise ValueError("contractions use the colliding (M = 1) sketch")
+    _need(h, "h", torch.int32, device)
+    _need(g, "g", torch.uint8, device)
+    if U.dim() == 1:
+        U = U.unsqueeze(0)
+    _need(U, "U", torch.float32, device)
+    L, n = U.shape
+    if h.shape != (B, 1, n):
+        raise ValueError(f"h must have shape [{B}][1][{n}]")
+    log2b = b.bit_length() - 1
+    return device, B, b, log2b, h, g, U, L, n
+
+
+def contract_iuu(FS: torch.Tensor, S: torch.Tensor, h: torch.Tensor, g: torch.Tensor,
+                 U: torch.Tensor, return_all: bool = False):
+    """Sketched T^(I,u,u) of every row of U (App. B, Eq. 14); median over the B sketches.
+    Returns Vmed [L][n] (and Vall [L][B][n] with return_all)."""
+    device, B, b, log2b, h, g, U, L, n = _contract_common(FS, S, h, g, U)
+    Vmed = torch.empty((L, n), dtype=torch.float32, device=device)
+    Vall = torch.empty((L, B, n), dtype=torch.float32, device=device) if return_all else None
+    rc = _lib.load().contract_iuu(_ctx(device), _ptr(FS), _ptr(S), _ptr(h), _ptr(g), B, log2b,
+                                  _ptr(U), L, n, _ptr(Vmed), _ptr(Vall))
+    _lib.check("contract_iuu", rc)
+    return (Vmed, Vall) if return_all else Vmed
+
+
+def contract_uuu(FS: torch.Tensor, S: torch.Tensor, h: torch.Tensor, g: torch.Tensor,
+                 U: torch.Tensor, return_all: bool = False):
+    """Sketched T^(u,u,u) of every row of U (App. B, Eq. 13); median over the B sketches."""
+    device, B, b, log2b, h, g, U, L, n = _contract_common(FS, S, h, g, U)
+    lam = torch.empty((L,), dtype=torch.float32, device=device)
+    lam_all = torch.empty((L, B), dtype=torch.float32, device=device) if return_all else None
+    rc = _lib.load().contract_uuu(_ctx(device), _ptr(FS), _ptr(S), _ptr(h), _ptr(g), B, log2b,
+                                  _ptr(U), L, n, _ptr(lam), _ptr(lam_all))
+    _lib.check("contract_uuu", rc)
+    return (lam, lam_all) if return_all else lam
+
+
+def robust_power_method(S: torch.Tensor, h: torch.Tensor, g: torch.Tensor, U0: torch.Tensor,
+                        T: int, return_deflated: bool = False):
+    """Alg. 1 on B colliding sketches S [B][b] (time domain) with initial vectors U0 [k][L][n].
+    Returns dict(lam [k] float64, V [k][n], tau [k] int32[, S_deflated [B][b]])."""
+    device = S.device
+    _need(S, "S", torch.complex64, device)
+    B, b = S.shape
+    h, g = _hashes_shape(h, g)
+    _need(h, "h", torch.int32, device)
+    _need(g, "g", torch.uint8, device)
+    _need(U0, "U0", torch.float32, device)
+    k, L, n = U0.shape
+    if h.shape != (B, 1, n):
+        raise ValueError(f"h must have shape [{B}][1][{n}]")
+    log2b = b.bit_length() - 1
+    lam = torch.empty((k,), dtype=torch.float64, device=device)
+    V = torch.empty((k, n), dtype=torch.float32, device=device)
+    tau = torch.empty((k,), dtype=torch.int32, device=device)
+    Sd = torch.empty_like(S) if return_deflated else None
+    rc = _lib.load().robust_power_method(_ctx(device), _ptr(S), _ptr(h), _ptr(g), B, log2b, n, k,
+                                         L, int(T), _ptr(U0), _ptr(lam), _ptr(V), _ptr(tau),
+                                         _ptr(Sd))
+    _lib.check("robust_power_method", rc)
+    out = {"lam": lam, "V": V, "tau": tau}
+    if return_deflated:
+        out["S_deflated"] = Sd
+    return out
+
+
+# ------------------------------------------------------------------ end-to-end call
+def decompose_symmetric(T, k: int, L: int, T_iters: int, B: int, log2b: int, seed: int,
+                        U0, device="cuda"):
+    """One call from a host (or device) symmetric tensor to (lambda, V): hashes, colliding
+    sketches (Eq. 7) and Alg. 1.  Host inputs are copied to the device and the results are
+    copied back to the host when T was given on the host."""
+    device = torch.device(device)
+    host = T.device.type == "cpu"
+    Td = T.to(device, non_blocking=True) if host else T
+    U0d = U0.to(device, non_blocking=True) if U0.device.type == "cpu" else U0
+    n = Td.shape[0]
+    h, g = cs_hashes(seed, B, log2b, [n], device)
+    S = sketch_tensor(Td, h, g, log2b)
+    res = robust_power_method(S, h, g, U0d, T_iters)
+    if host:
+        return {key: val.to("cpu") for key, val in res.items()}
+    return res

@@ -1,0 +1,229 @@
+// Launchers and C entry points for the sketched contractions (contract_iuu, contract_uuu) and
+// the fast robust tensor power method (Alg. 1).
+#include <stdio.h>
+
+#include "contract.cuh"
+
+namespace tsk {
+
+template <int LOGB, int MODE>
+static int launch_contract_t(const ContractArgs& a, cudaStream_t st) {
+  constexpr int NT = threads_for_logb(LOGB);
+  constexpr size_t smem = contract_smem_bytes<LOGB>();
+  TSK_CUDA(cudaFuncSetAttribute(contract_kernel<LOGB, MODE>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(a.B, a.L);
+  contract_kernel<LOGB, MODE><<<grid, NT, smem, st>>>(a);
+  TSK_CHECK_LAUNCH();
+  return TSK_OK;
+}
+
+template <int LOGB>
+static int launch_contract_mode(int mode, const ContractArgs& a, cudaStream_t st) {
+  return mode == MODE_IUU ? launch_contract_t<LOGB, MODE_IUU>(a, st)
+                          : launch_contract_t<LOGB, MODE_UUU>(a, st);
+}
+
+int launch_contract(int log2b, int mode, const ContractArgs& a, cudaStream_t st) {
+  switch (log2b) {
+    case 8: return launch_contract_mode<8>(mode, a, st);
+    case 9: return launch_contract_mode<9>(mode, a, st);
+    case 10: return launch_contract_mode<10>(mode, a, st);
+    case 11: return launch_contract_mode<11>(mode, a, st);
+    case 12: return launch_contract_mode<12>(mode, a, st);
+    case 13: return launch_contract_mode<13>(mode, a, st);
+    case 14: return launch_contract_mode<14>(mode, a, st);
+    default: return TSK_EUNSUPPORTED;
+  }
+}
+
+template <int LOGB>
+static int launch_deflate_t(const DeflateArgs& a, cudaStream_t st) {
+  constexpr int NT = threads_for_logb(LOGB);
+  constexpr size_t smem = deflate_smem_bytes<LOGB>();
+  TSK_CUDA(cudaFuncSetAttribute(deflate_kernel<LOGB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  deflate_kernel<LOGB><<<a.B, NT, smem, st>>>(a);
+  TSK_CHECK_LAUNCH();
+  return TSK_OK;
+}
+
+int launch_deflate(int log2b, const DeflateArgs& a, cudaStream_t st) {
+  switch (log2b) {
+    case 8: return launch_deflate_t<8>(a, st);
+    case 9: return launch_deflate_t<9>(a, st);
+    case 10: return launch_deflate_t<10>(a, st);
+    case 11: return launch_deflate_t<11>(a, st);
+    case 12: return launch_deflate_t<12>(a, st);
+    case 13: return launch_deflate_t<13>(a, st);
+    case 14: return launch_deflate_t<14>(a, st);
+    default: return TSK_EUNSUPPORTED;
+  }
+}
+
+int launch_fft_batched(int log2b, const float2* in, float2* out, int B, int inverse, cudaStream_t st);
+
+}  // namespace tsk
+
+using namespace tsk;
+
+static int check_contract_args(tsk_ctx* ctx, const float* FS, const float* S, const int32_t* h,
+                               const uint8_t* g, int B, int log2b, const float* U, int L, int64_t n) {
+  if (!ctx || !FS || !S || !h || !g || !U) return TSK_EINVAL;
+  if (B < 1 || L < 1 || n < 1) return TSK_EINVAL;
+  if (log2b < 1 || log2b > 24) return TSK_EINVAL;
+  if (log2b < 8 || log2b > 14 || B > kMaxB || n > 8192 || L > 65535) return TSK_EUNSUPPORTED;
+  return TSK_OK;
+}
+
+extern "C" int contract_iuu(tsk_ctx* ctx, const float* FS, const float* S, const int32_t* h,
+                            const uint8_t* g, int B, int log2b, const float* U, int L, int64_t n,
+                            float* Vmed, float* Vall) {
+  int rc = check_contract_args(ctx, FS, S, h, g, B, log2b, U, L, n);
+  if (rc != TSK_OK) return rc;
+  if (!Vmed) return TSK_EINVAL;
+  const size_t vall_bytes = Vall ? 0 : ws_round((size_t)L * B * n * sizeof(float));
+  const size_t need = vall_bytes + ws_round((size_t)L * B * sizeof(float)) +
+                      ws_round((size_t)L * sizeof(unsigned));
+  if ((rc = tsk_ws_reserve(ctx, need)) != TSK_OK) return rc;
+  WsCarve wc{static_cast<char*>(ctx->ws), 0};
+  ContractArgs a{};
+  a.Vall = Vall ? Vall : wc.take<float>((size_t)L * B * n);
+  a.lam_all = wc.take<float>((size_t)L * B);
+  a.counters = wc.take<unsigned>(L);
+  TSK_CUDA(cudaMemsetAsync(a.counters, 0, L * sizeof(unsigned), ctx->stream));
+  a.FS = reinterpret_cast<const float2*>(FS);
+  a.S = reinterpret_cast<const float2*>(S);
+  a.h = h;
+  a.g = g;
+  a.U = U;
+  a.n = (int)n;
+  a.B = B;
+  a.L = L;
+  a.normalize_input = 0;
+  a.Vmed = Vmed;
+  a.Unext = nullptr;
+  a.lam_med = nullptr;
+  a.status = ctx->status;
+  return launch_contract(log2b, MODE_IUU, a, ctx->stream);
+}
+
+extern "C" int contract_uuu(tsk_ctx* ctx, const float* FS, const float* S, const int32_t* h,
+                            const uint8_t* g, int B, int log2b, const float* U, int L, int64_t n,
+                            float* lam_med, float* lam_all) {
+  int rc = check_contract_args(ctx, FS, S, h, g, B, log2b, U, L, n);
+  if (rc != TSK_OK) return rc;
+  if (!lam_med) return TSK_EINVAL;
+  const size_t need = (lam_all ? 0 : ws_round((size_t)L * B * sizeof(float))) +
+                      ws_round((size_t)L * sizeof(unsigned));
+  if ((rc = tsk_ws_reserve(ctx, need)) != TSK_OK) return rc;
+  WsCarve wc{static_cast<char*>(ctx->ws), 0};
+  ContractArgs a{};
+  a.lam_all = lam_all ? lam_all : wc.take<float>((size_t)L * B);
+  a.counters = wc.take<unsigned>(L);
+  TSK_CUDA(cudaMemsetAsync(a.counters, 0, L * sizeof(unsigned), ctx->stream));
+  a.FS = reinterpret_cast<const float2*>(FS);
+  a.S = reinterpret_cast<const float2*>(S);
+  a.h = h;
+  a.g = g;
+  a.U = U;
+  a.n = (int)n;
+  a.B = B;
+  a.L = L;
+  a.normalize_input = 0;
+  a.Vall = nullptr;
+  a.Vmed = nullptr;
+  a.Unext = nullptr;
+  a.lam_med = lam_med;
+  a.status = ctx->status;
+  return launch_contract(log2b, MODE_UUU, a, ctx->stream);
+}
+
+extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* h,
+                                   const uint8_t* g, int B, int log2b, int64_t n, int k, int L,
+                                   int T, const float* U0, double* lambda, float* Vout,
+                                   int32_t* tau_star, float* S_deflated) {
+  if (!ctx || !S || !h || !g) return TSK_EINVAL;
+  if (k < 0 || T < 0 || B < 1 || L < 1 || n < 1) return TSK_EINVAL;
+  if (log2b < 1 || log2b > 24) return TSK_EINVAL;
+  if (log2b < 8 || log2b > 14 || B > kMaxB || n > 8192 || L > 4096 || T < 1)
+    return TSK_EUNSUPPORTED;
+  if (k == 0) {
+    if (S_deflated && S_deflated != S)
+      TSK_CUDA(cudaMemcpyAsync(S_deflated, S, (size_t)B * (1 << log2b) * sizeof(float2),
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+    return TSK_OK;
+  }
+  if (!U0 || !lambda || !Vout) return TSK_EINVAL;
+  const size_t b = (size_t)1 << log2b;
+  const size_t need = 2 * ws_round(B * b * sizeof(float2)) + ws_round((size_t)L * B * n * 4) +
+                      ws_round((size_t)L * B * 4) + 2 * ws_round((size_t)L * n * 4) +
+                      ws_round((size_t)L * 4) + ws_round((size_t)L * 4);
+  int rc = tsk_ws_reserve(ctx, need);
+  if (rc != TSK_OK) return rc;
+  WsCarve wc{static_cast<char*>(ctx->ws), 0};
+  float2* Sw = wc.take<float2>(B * b);
+  float2* FSw = wc.take<float2>(B * b);
+  float* Vall = wc.take<float>((size_t)L * B * n);
+  float* lam_all = wc.take<float>((size_t)L * B);
+  float* Ua = wc.take<float>((size_t)L * n);
+  float* Ub = wc.take<float>((size_t)L * n);
+  float* lam_med = wc.take<float>(L);
+  unsigned* counters = wc.take<unsigned>(L);
+  cudaStream_t st = ctx->stream;
+  TSK_CUDA(cudaMemsetAsync(counters, 0, L * sizeof(unsigned), st));
+  TSK_CUDA(cudaMemcpyAsync(Sw, S, B * b * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+  if ((rc = launch_fft_batched(log2b, Sw, FSw, B, 0, st)) != TSK_OK) return rc;
+
+  ContractArgs a{};
+  a.FS = FSw;
+  a.S = Sw;
+  a.h = h;
+  a.g = g;
+  a.n = (int)n;
+  a.B = B;
+  a.L = L;
+  a.Vall = Vall;
+  a.lam_all = lam_all;
+  a.counters = counters;
+  a.status = ctx->status;
+  DeflateArgs d{};
+  d.FS = FSw;
+  d.S = Sw;
+  d.h = h;
+  d.g = g;
+  d.n = (int)n;
+  d.B = B;
+  d.L = L;
+  d.lam_med = lam_med;
+  d.lambda_out = lambda;
+  d.Vout = Vout;
+  d.tau_out = tau_star;
+
+  for (int r = 0; r < k; ++r) {
+    const float* cur = U0 + (size_t)r * L * n;
+    float* bufs[2] = {Ua, Ub};
+    for (int t = 0; t < T; ++t) {
+      a.U = cur;
+      a.normalize_input = (t == 0);
+      a.Unext = bufs[t & 1];
+      a.Vmed = nullptr;
+      a.lam_med = nullptr;
+      if ((rc = launch_contract(log2b, MODE_IUU, a, st)) != TSK_OK) return rc;
+      cur = bufs[t & 1];
+    }
+    // selection: lambda_tau = median_m T^(m)(u_tau, u_tau, u_tau)
+    a.U = cur;
+    a.normalize_input = 0;
+    a.Unext = nullptr;
+    a.Vmed = nullptr;
+    a.lam_med = lam_med;
+    if ((rc = launch_contract(log2b, MODE_UUU, a, st)) != TSK_OK) return rc;
+    d.Ucur = cur;
+    d.round = r;
+    if ((rc = launch_deflate(log2b, d, st)) != TSK_OK) return rc;
+  }
+  if (S_deflated)
+    TSK_CUDA(cudaMemcpyAsync(S_deflated, Sw, B * b * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+  return TSK_OK;
+}

@@ -1,0 +1,181 @@
+// Block-wide power-of-two FFTs over shared memory (Stockham auto-sort, radix <= 16).
+//
+// The DFTs of Eq. 4 and Prop. 1 are computed by one thread block per transform.  The data live
+// in shared memory in the padded layout of pad_idx(); each pass loads E = N/NT elements per
+// thread into registers, applies twiddles and radix-R DFTs in registers, synchronises, and
+// stores to the Stockham output positions -- so transforms run in place without a second
+// buffer.  Output is in natural order.  DIR = -1 is the forward transform exp(-2 pi i f t/N),
+// DIR = +1 the unnormalised inverse (callers apply 1/N).
+//
+// Pass structure (Stockham auto-sort): with NS = product of the radices already applied,
+// butterfly j reads x[j + r N/R] (r < R), multiplies element r by w_{NS R}^{DIR r (j mod NS)},
+// takes an R-point DFT and writes element r to x[(j / NS) NS R + (j mod NS) + r NS].
+#pragma once
+
+#include "common.cuh"
+
+namespace tsk {
+
+// z * (DIR * i)
+template <int DIR>
+TSK_HD float2 mul_dir_i(float2 z) {
+  return DIR > 0 ? make_float2(-z.y, z.x) : make_float2(z.y, -z.x);
+}
+
+// z * (c + DIR * s * i) for constants c, s
+template <int DIR>
+TSK_HD float2 mul_const(float2 z, float c, float s) {
+  const float sd = DIR > 0 ? s : -s;
+  return make_float2(z.x * c - z.y * sd, z.x * sd + z.y * c);
+}
+
+// cos and sin of pi/8, pi/4 (exact decimal expansions of the mathematical constants)
+#define TSK_C8 0.92387953251128675613f
+#define TSK_S8 0.38268343236508977173f
+#define TSK_R2 0.70710678118654752440f
+
+// z * w16^e with w16 = exp(DIR 2 pi i / 16), e in [0, 8); e is a compile-time constant after
+// unrolling, so the branches fold away.
+template <int DIR>
+TSK_HD float2 mul_w16(float2 z, int e) {
+  switch (e) {
+    case 0: return z;
+    case 1: return mul_const<DIR>(z, TSK_C8, TSK_S8);
+    case 2: return mul_const<DIR>(z, TSK_R2, TSK_R2);
+    case 3: return mul_const<DIR>(z, TSK_S8, TSK_C8);
+    case 4: return mul_dir_i<DIR>(z);
+    case 5: return mul_const<DIR>(z, -TSK_S8, TSK_C8);
+    case 6: return mul_const<DIR>(z, -TSK_R2, TSK_R2);
+    default: return mul_const<DIR>(z, -TSK_C8, TSK_S8);
+  }
+}
+
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+__host__ __device__ constexpr int bitrev(int x, int bits) {
+  return bits == 0 ? 0 : ((x & 1) << (bits - 1)) | bitrev(x >> 1, bits - 1);
+}
+
+// In-place radix-2 decimation-in-frequency DFT of R <= 16 points held in registers.
+// X_s = sum_r v_r exp(DIR 2 pi i r s / R) ends up in v[bitrev(s, log2 R)].
+template <int R, int DIR>
+TSK_HD void dft_dif(float2* v) {
+  static_assert(R == 2 || R == 4 || R == 8 || R == 16, "radix");
+#pragma unroll
+  for (int span = R / 2; span >= 1; span /= 2) {
+#pragma unroll
+    for (int gbase = 0; gbase < R; gbase += 2 * span) {
+#pragma unroll
+      for (int s = 0; s < span; ++s) {
+        const float2 a = v[gbase + s], c = v[gbase + s + span];
+        v[gbase + s] = cadd(a, c);
+        v[gbase + s + span] = mul_w16<DIR>(csub(a, c), s * (8 / span));
+      }
+    }
+  }
+}
+
+// exp(DIR * 2 pi i * k / span), span a power of two.
+TSK_HD float2 unit_root(int k, int span, int dir) {
+#ifdef __CUDA_ARCH__
+  float s, c;
+  sincospif((float)(2 * k) / (float)span, &s, &c);
+  return make_float2(c, dir > 0 ? s : -s);
+#else
+  const double a = 2.0 * 3.14159265358979323846 * (double)k / (double)span;
+  return make_float2((float)cos(a), (float)(dir > 0 ? sin(a) : -sin(a)));
+#endif
+}
+
+// v[r] *= w^r, w = exp(DIR 2 pi i k / span), r = 1..R-1.  w^2, w^4, w^8 are formed by
+// squaring and the odd powers by one extra product, so at most four roundings separate any
+// power from the correctly rounded w.
+template <int R, int DIR>
+TSK_HD void twiddle(float2* v, int k, int span) {
+  const float2 w1 = unit_root(k, span, DIR);
+  v[1] = cmul(v[1], w1);
+  if constexpr (R >= 4) {
+    const float2 w2 = cmul(w1, w1);
+    v[2] = cmul(v[2], w2);
+    v[3] = cmul(v[3], cmul(w2, w1));
+    if constexpr (R >= 8) {
+      const float2 w4 = cmul(w2, w2);
+      v[4] = cmul(v[4], w4);
+      v[5] = cmul(v[5], cmul(w4, w1));
+      const float2 w6 = cmul(w4, w2);
+      v[6] = cmul(v[6], w6);
+      v[7] = cmul(v[7], cmul(w6, w1));
+      if constexpr (R >= 16) {
+        const float2 w8 = cmul(w4, w4);
+#pragma unroll
+        for (int r = 8; r < 16; ++r) {
+          float2 t = w8;
+          if (r & 4) t = cmul(t, w4);
+          if (r & 2) t = cmul(t, w2);
+          if (r & 1) t = cmul(t, w1);
+          v[r] = cmul(v[r], t);
+        }
+      }
+    }
+  }
+}
+
+template <int N, int NT, int R, int NS, int DIR>
+struct StockhamPass {
+  static constexpr int E = N / NT;
+  static constexpr int NB = E / R;
+  static_assert(NB * R == E, "elements per thread must be a multiple of the radix");
+
+  static TSK_HD void load_compute(const float2* x, int tid, float2* v) {
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int j = tid + q * NT;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q * R + r] = x[pad_idx(j + r * (N / R))];
+      if constexpr (NS > 1) twiddle<R, DIR>(v + q * R, j & (NS - 1), NS * R);
+      dft_dif<R, DIR>(v + q * R);
+    }
+  }
+  static TSK_HD void store(float2* x, int tid, const float2* v) {
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int j = tid + q * NT;
+      const int k = j & (NS - 1);
+      const int base = (j / NS) * NS * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[pad_idx(base + r * NS)] = v[q * R + bitrev(r, ilog2(R))];
+    }
+  }
+};
+
+template <int N, int NT, int NS, int DIR>
+struct FftPasses {
+  static constexpr int E = N / NT;
+  static constexpr int REM = N / NS;
+  static constexpr int R = REM >= E ? E : REM;
+  static __device__ __forceinline__ void run(float2* x) {
+    float2 v[E];
+    StockhamPass<N, NT, R, NS, DIR>::load_compute(x, threadIdx.x, v);
+    __syncthreads();
+    StockhamPass<N, NT, R, NS, DIR>::store(x, threadIdx.x, v);
+    __syncthreads();
+    if constexpr (NS * R < N) FftPasses<N, NT, NS * R, DIR>::run(x);
+  }
+};
+
+// In-place FFT of N = 2^LOGN complex values at x (padded layout) by a block of exactly NT
+// threads.  Must be called by all NT threads; begins and ends with the data synchronised.
+template <int LOGN, int NT, int DIR>
+__device__ __forceinline__ void block_fft(float2* x) {
+  constexpr int N = 1 << LOGN;
+  constexpr int E = N / NT;
+  static_assert(E >= 2 && E <= 16 && (E & (E - 1)) == 0, "2..16 elements per thread");
+  FftPasses<N, NT, 1, DIR>::run(x);
+}
+
+// Threads per block used by the sketch-length-b kernels: b/16 (16 elements per thread for a
+// length-b transform, 8 for a length-b/2 one), at least one warp, at most 1024.
+constexpr int threads_for_logb(int logb) {
+  return (1 << logb) / 16 < 32 ? 32 : ((1 << logb) / 16 > 1024 ? 1024 : (1 << logb) / 16);
+}
+
+}  // namespace tsk

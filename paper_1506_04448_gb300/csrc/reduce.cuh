@@ -1,0 +1,48 @@
+// Warp and block reductions, and the small-sample median used for the B sketches.
+#pragma once
+
+#include "common.cuh"
+
+namespace tsk {
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over a block of NT threads (NT a multiple of 32).  `red` holds >= 33 floats of shared
+// memory.  Every thread receives the total; `red` may be reused after return.
+template <int NT>
+__device__ __forceinline__ float block_sum(float v, float* red) {
+  static_assert(NT % 32 == 0, "block of whole warps");
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float r = (threadIdx.x < NT / 32) ? red[threadIdx.x] : 0.f;
+    r = warp_sum(r);
+    if (threadIdx.x == 0) red[32] = r;
+  }
+  __syncthreads();
+  const float total = red[32];
+  __syncthreads();
+  return total;
+}
+
+// Median of x[0..cnt) (cnt >= 1) by insertion sort in place; mean of the two middle values
+// when cnt is even (the even-B reading of Alg. 1's median).
+__device__ __forceinline__ float small_median(float* x, int cnt) {
+  for (int a = 1; a < cnt; ++a) {
+    const float key = x[a];
+    int c = a - 1;
+    while (c >= 0 && x[c] > key) {
+      x[c + 1] = x[c];
+      --c;
+    }
+    x[c + 1] = key;
+  }
+  return (cnt & 1) ? x[cnt / 2] : 0.5f * (x[cnt / 2 - 1] + x[cnt / 2]);
+}
+
+}  // namespace tsk

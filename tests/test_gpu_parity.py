@@ -1,0 +1,280 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on identical seeded inputs.
+
+Tolerances: integer work (hash tables, int64 sketches) bit-exact; FP32 sketches, DFTs and
+contraction vectors within 1e-5 relative in the 2-norm per (vector, sketch); recovered
+eigenvalues and components within 1e-4.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+tsk = pytest.importorskip("paper_1506_04448_gb300")
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def t32(x, dev):
+    return torch.tensor(np.asarray(x), dtype=torch.float32, device=dev)
+
+
+# ------------------------------------------------------------------ hashing
+@pytest.mark.parametrize("seed,B,log2b,dims", [
+    (1, 2, 10, [3, 5, 4]), (7, 5, 10, [50]), (2**63 + 5, 3, 14, [400]), (0, 1, 8, [1]),
+    (123, 4, 15, [500, 400, 300]), (99, 64, 12, [33])])
+def test_hashes_bit_exact(dev, seed, B, log2b, dims):
+    h, g = tsk.cs_hashes(seed, B, log2b, dims, dev)
+    ho, go = O.cs_hashes(seed, B, log2b, dims)
+    np.testing.assert_array_equal(h.cpu().numpy(), ho)
+    np.testing.assert_array_equal(g.cpu().numpy(), go)
+
+
+# ------------------------------------------------------------------ sketch construction
+@pytest.mark.parametrize("n,log2b,B", [(1, 8, 1), (9, 8, 3), (30, 10, 2), (65, 12, 4)])
+def test_symmetric_int_sketch_bit_exact(dev, n, log2b, B):
+    b = 1 << log2b
+    Ti = synth.random_symmetric_int(n, 100 + n)
+    h, g = tsk.cs_hashes(11 + n, B, log2b, [n], dev)
+    S = tsk.sketch_tensor(torch.tensor(Ti, device=dev), h, g, log2b, acc="ci64").cpu().numpy()
+    ho, go = O.cs_hashes(11 + n, B, log2b, [n])
+    for m in range(B):
+        ref = O.sketch_tensor_sym(Ti, ho[m, 0], go[m, 0], b)
+        np.testing.assert_array_equal(S[m, :, 0], ref[0])
+        np.testing.assert_array_equal(S[m, :, 1], ref[1])
+
+
+@pytest.mark.parametrize("n,log2b,B", [(5, 8, 2), (37, 10, 3), (100, 14, 2)])
+def test_symmetric_float_sketch(dev, n, log2b, B):
+    b = 1 << log2b
+    T = synth.random_symmetric(n, 200 + n)
+    h, g = tsk.cs_hashes(3 + n, B, log2b, [n], dev)
+    ho, go = O.cs_hashes(3 + n, B, log2b, [n])
+    S32 = tsk.sketch_tensor(t32(T, dev), h, g, log2b).cpu().numpy()
+    S64 = tsk.sketch_tensor(torch.tensor(T, device=dev), h, g, log2b, acc="c128").cpu().numpy()
+    T32 = T.astype(np.float32).astype(np.float64)
+    for m in range(B):
+        assert rel(S32[m], O.sketch_tensor_sym(T32, ho[m, 0], go[m, 0], b)) < 1e-5
+        assert rel(S64[m], O.sketch_tensor_sym(T, ho[m, 0], go[m, 0], b)) < 1e-12
+
+
+def test_sketch_accumulate_is_linear(dev):
+    n, log2b, B = 20, 10, 2
+    A = synth.random_symmetric(n, 1)
+    C = synth.random_symmetric(n, 2)
+    h, g = tsk.cs_hashes(5, B, log2b, [n], dev)
+    S = tsk.sketch_tensor(t32(A, dev), h, g, log2b)
+    S = tsk.sketch_tensor(t32(C, dev), h, g, log2b, S=S, accumulate=True)
+    R = tsk.sketch_tensor(t32(A + C, dev), h, g, log2b)
+    assert rel(S.cpu().numpy(), R.cpu().numpy()) < 1e-5
+
+
+@pytest.mark.parametrize("dims,log2b", [((7, 5, 3), 8), ((40, 33, 29), 12), ((50, 40, 30), 15)])
+def test_asymmetric_sketch(dev, dims, log2b):
+    b = 1 << log2b
+    r = synth.rng(sum(dims))
+    T = r.standard_normal(dims)
+    Ti = r.integers(-500, 500, size=dims).astype(np.int32)
+    h, g = tsk.cs_hashes(17, 2, log2b, list(dims), dev)
+    ho, go = O.cs_hashes(17, 2, log2b, list(dims))
+    S = tsk.sketch_tensor(t32(T, dev), h, g, log2b).cpu().numpy()
+    T32 = T.astype(np.float32).astype(np.float64)
+    for m in range(2):
+        assert rel(S[m], O.sketch_tensor_asym(T32, ho[m], go[m], b)) < 1e-5
+    if log2b <= 14:
+        Si = tsk.sketch_tensor(torch.tensor(Ti, device=dev), h, g, log2b, acc="ci64").cpu().numpy()
+        for m in range(2):
+            np.testing.assert_array_equal(Si[m, :, 0], O.sketch_tensor_asym(Ti, ho[m], go[m], b))
+            assert not Si[m, :, 1].any()
+
+
+# ------------------------------------------------------------------ DFT
+@pytest.mark.parametrize("log2b", [8, 9, 10, 11, 12, 13, 14])
+def test_sketch_fft(dev, log2b):
+    b = 1 << log2b
+    r = synth.rng(log2b)
+    X = r.standard_normal((3, b)) + 1j * r.standard_normal((3, b))
+    Xd = torch.tensor(X, dtype=torch.complex64, device=dev)
+    F = tsk.sketch_fft(Xd).cpu().numpy()
+    Xi = tsk.sketch_fft(Xd, inverse=True).cpu().numpy()
+    X32 = Xd.cpu().numpy().astype(np.complex128)
+    for m in range(3):
+        assert rel(F[m], O.conv.fft(X32[m])) < 2e-6
+        assert rel(Xi[m], O.conv.ifft(X32[m])) < 2e-6
+
+
+# ------------------------------------------------------------------ rank-1 sketches
+@pytest.mark.parametrize("domain", ["time", "freq"])
+def test_sketch_rank1_symmetric(dev, domain):
+    n, log2b, B, cnt = 30, 10, 3, 4
+    b = 1 << log2b
+    U = synth.rng(3).standard_normal((cnt, n))
+    w = np.array([1.0, -0.5, 2.0, 0.25])
+    h, g = tsk.cs_hashes(21, B, log2b, [n], dev)
+    ho, go = O.cs_hashes(21, B, log2b, [n])
+    S = tsk.sketch_rank1(t32(w, dev), t32(U, dev), h, g, log2b, domain=domain).cpu().numpy()
+    U32 = U.astype(np.float32).astype(np.float64)
+    for m in range(B):
+        ref = sum(w[c] * O.sketch_rank1_sym(U32[c], ho[m, 0], go[m, 0], b) for c in range(cnt))
+        if domain == "freq":
+            ref = O.conv.fft(ref)
+        assert rel(S[m], ref) < 1e-5
+
+
+def test_sketch_rank1_asymmetric_and_accumulate(dev):
+    dims, log2b, B = (9, 7, 5), 9, 2
+    b = 1 << log2b
+    r = synth.rng(4)
+    U, V, W = (r.standard_normal((2, d)) for d in dims)
+    w = np.array([0.7, -1.3])
+    h, g = tsk.cs_hashes(23, B, log2b, list(dims), dev)
+    ho, go = O.cs_hashes(23, B, log2b, list(dims))
+    S0 = torch.zeros((B, b), dtype=torch.complex64, device=dev)
+    S0[:, 3] = 1.0
+    S = tsk.sketch_rank1(t32(w, dev), t32(U, dev), h, g, log2b, V=t32(V, dev), W=t32(W, dev),
+                         S=S0, accumulate=True).cpu().numpy()
+    f = lambda x: x.astype(np.float32).astype(np.float64)  # noqa: E731
+    for m in range(B):
+        ref = sum(w[c] * O.sketch_rank1_asym(f(U[c]), f(V[c]), f(W[c]), ho[m], go[m], b) for c in range(2))
+        ref[3] += 1.0
+        assert rel(S[m], ref) < 1e-5
+
+
+# ------------------------------------------------------------------ contractions
+def _sketches(dev, n, log2b, B, seed, noise=0.1, k=3):
+    T, _, _ = synth.planted_symmetric(n, k, noise, seed)
+    h, g = tsk.cs_hashes(seed, B, log2b, [n], dev)
+    S = tsk.sketch_tensor(t32(T, dev), h, g, log2b)
+    FS = tsk.sketch_fft(S)
+    ho, go = O.cs_hashes(seed, B, log2b, [n])
+    return T, h, g, S, FS, ho, go
+
+
+@pytest.mark.parametrize("n,log2b,B,L", [(5, 8, 1, 1), (37, 10, 2, 3), (64, 12, 5, 2),
+                                         (33, 13, 4, 2), (400, 14, 10, 3)])
+def test_contract_iuu_and_uuu(dev, n, log2b, B, L):
+    b = 1 << log2b
+    _, h, g, S, FS, ho, go = _sketches(dev, n, log2b, B, 31 + n)
+    U = synth.rng(n).standard_normal((L, n))
+    U /= np.linalg.norm(U, axis=1, keepdims=True)
+    Ud = t32(U, dev)
+    Vmed, Vall = tsk.contract_iuu(FS, S, h, g, Ud, return_all=True)
+    lam, lam_all = tsk.contract_uuu(FS, S, h, g, Ud, return_all=True)
+    Sg = S.cpu().numpy().astype(np.complex128)
+    Ug = Ud.cpu().numpy().astype(np.float64)
+    Vall = Vall.cpu().numpy()
+    lam_all = lam_all.cpu().numpy()
+    for tau in range(L):
+        refs = np.stack([O.contract_iuu(Sg[m], Ug[tau], ho[m, 0], go[m, 0], b, "fft") for m in range(B)])
+        lrefs = np.array([O.contract_uuu(Sg[m], Ug[tau], ho[m, 0], go[m, 0], b, "fft") for m in range(B)])
+        for m in range(B):
+            assert rel(Vall[tau, m], refs[m]) < 1e-5, (tau, m)
+        assert rel(Vmed[tau].cpu().numpy(), O.median_rows(refs)) < 1e-5
+        scale = np.linalg.norm(refs) / np.sqrt(B)
+        assert np.max(np.abs(lam_all[tau] - lrefs)) < 1e-5 * max(scale, 1e-30)
+        assert abs(lam[tau].item() - O.median(lrefs)) < 1e-5 * max(scale, 1e-30)
+        # per-sketch invariant T^(u,u,u) = <u, T^(I,u,u)> (App. B)
+        assert np.max(np.abs(Vall[tau] @ Ug[tau] - lam_all[tau])) < 1e-5 * max(scale, 1e-30)
+
+
+def test_contract_collision_free_is_exact(dev):
+    n = 4
+    b = 256
+    T = synth.random_symmetric(n, 5)
+    hv = np.array([4 ** i for i in range(n)], dtype=np.int32)
+    h = torch.tensor(np.stack([hv, hv]), dtype=torch.int32, device=dev)
+    gv = np.array([[0, 1, 2, 3], [3, 1, 0, 2]])
+    g = torch.tensor(gv, dtype=torch.uint8, device=dev)
+    S = tsk.sketch_tensor(t32(T, dev), h, g, 8)
+    FS = tsk.sketch_fft(S)
+    U = synth.rng(6).standard_normal((2, n))
+    Ud = t32(U, dev)
+    V = tsk.contract_iuu(FS, S, h, g, Ud).cpu().numpy()
+    lam = tsk.contract_uuu(FS, S, h, g, Ud).cpu().numpy()
+    T32 = T.astype(np.float32).astype(np.float64)
+    Ug = Ud.cpu().numpy().astype(np.float64)
+    for tau in range(2):
+        assert rel(V[tau], O.exact_iuu(T32, Ug[tau])) < 1e-5
+        assert abs(lam[tau] - O.exact_uuu(T32, Ug[tau])) < 1e-5 * np.linalg.norm(T32.ravel())
+
+
+# ------------------------------------------------------------------ Alg. 1
+def _follow_rtpm(dev, n, k, L, T_it, B, log2b, seed, noise):
+    b = 1 << log2b
+    T, lam_true, A = synth.planted_symmetric(n, k, noise, seed)
+    U0 = synth.gaussian_inits(k, L, n, seed + 1)
+    h, g = tsk.cs_hashes(seed, B, log2b, [n], dev)
+    S = tsk.sketch_tensor(t32(T, dev), h, g, log2b)
+    res = tsk.robust_power_method(S, h, g, t32(U0, dev), T_it, return_deflated=True)
+    tsk.check_status(dev)
+    ho, go = O.cs_hashes(seed, B, log2b, [n])
+    Sg = S.cpu().numpy().astype(np.complex128)
+    U0g = t32(U0, dev).cpu().numpy().astype(np.float64)
+    tau = res["tau"].cpu().numpy()
+    ref = O.rtpm_sketched(Sg, ho[:, 0], go[:, 0], b, U0g, T_it, "fft", tau_choice=tau)
+    return res, ref, lam_true, A
+
+
+def test_rtpm_small_config_parity(dev):
+    """n = 50, k = 5, B = 5, b = 2^10, L = 10, T = 20 (the small planted configuration)."""
+    res, ref, lam_true, A = _follow_rtpm(dev, 50, 5, 10, 20, 5, 10, 1, 0.01)
+    lam = res["lam"].cpu().numpy()
+    V = res["V"].cpu().numpy()
+    tau = res["tau"].cpu().numpy()
+    for r in range(5):
+        # the GPU's choice is an argmax of the oracle's eigenvalues up to the tolerance
+        assert ref["lam_all"][r, tau[r]] >= ref["lam_all"][r].max() - 1e-4 * abs(ref["lam_all"][r].max())
+        assert abs(lam[r] - ref["lam"][r]) <= 1e-4 * max(1.0, abs(ref["lam"][r]))
+        assert np.linalg.norm(V[r] - ref["V"][r]) <= 1e-4
+    Sd = res["S_deflated"].cpu().numpy()
+    assert rel(Sd, ref["S_deflated"]) < 1e-4
+
+
+def test_rtpm_recovers_planted_components_at_large_b(dev):
+    """Noise-free planted tensor, b = 2^14: the sketched method finds the components (Thm. 2)."""
+    n, k = 20, 3
+    res, ref, lam_true, A = _follow_rtpm(dev, n, k, 8, 15, 5, 14, 3, 0.0)
+    lam = res["lam"].cpu().numpy()
+    V = res["V"].cpu().numpy()
+    order = np.argsort(-lam_true)
+    for r in range(k):
+        a = A[:, order[r]]
+        assert abs(lam[r] - lam_true[order[r]]) < 0.1
+        assert min(np.linalg.norm(V[r] - a), np.linalg.norm(V[r] + a)) < 0.1
+
+
+def test_rtpm_reports_nonfinite(dev):
+    n, B, log2b = 10, 2, 8
+    h, g = tsk.cs_hashes(1, B, log2b, [n], dev)
+    S = tsk.sketch_tensor(t32(synth.random_symmetric(n, 1), dev), h, g, log2b)
+    U0 = torch.zeros((1, 2, n), dtype=torch.float32, device=dev)
+    tsk.robust_power_method(S, h, g, U0, 2)
+    assert tsk.ctx_status(dev) == -5   # TSK_ENONFINITE
+    assert tsk.ctx_status(dev) == 0    # cleared
+
+
+def test_argument_errors(dev):
+    h, g = tsk.cs_hashes(1, 2, 8, [10], dev)
+    S = torch.zeros((2, 256), dtype=torch.complex64, device=dev)
+    with pytest.raises(tsk.TskError, match="EUNSUPPORTED"):
+        tsk.robust_power_method(S, h, g, torch.ones((1, 1, 10), device=dev), 0)
+    Sbig = torch.zeros((2, 1 << 15), dtype=torch.complex64, device=dev)
+    with pytest.raises(tsk.TskError, match="EUNSUPPORTED"):
+        tsk.contract_iuu(Sbig, Sbig, h, g, torch.ones((1, 10), device=dev))
+    with pytest.raises(TypeError):
+        tsk.contract_iuu(S, S, h, g, torch.ones((1, 10), device=dev, dtype=torch.float64))
