@@ -339,8 +339,41 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile(args):
+    """A small, fixed launch sequence for ncu captures of the benchmarked kernels:
+    'contract' -- 6 launches of the fused contraction kernel in the power-step shape (B x L);
+    'build'    -- 4 launches of the symmetric sketch build on the n = 400 tensor;
+    'rtpm'     -- 2 full steps (hashes, build, Alg. 1), the first one a warm-up."""
+    import torch
+    import paper_1506_04448_gb300 as tsk
+    dev = torch.device("cuda:0")
+    cfg = dict(CFG)
+    n, B, log2b, L = cfg["n"], cfg["B"], cfg["log2b"], cfg["L"]
+    T_host, U0_host = make_inputs(cfg)
+    T_d = torch.from_numpy(T_host).to(dev)
+    U0_d = torch.from_numpy(U0_host).to(dev)
+    h, g = tsk.cs_hashes(cfg["seed"], B, log2b, [n], dev)
+    if args.profile == "build":
+        for _ in range(4):
+            tsk.sketch_tensor(T_d, h, g, log2b)
+    elif args.profile == "contract":
+        S = tsk.sketch_tensor(T_d, h, g, log2b)
+        FS = tsk.sketch_fft(S)
+        U = torch.nn.functional.normalize(U0_d[0], dim=1).contiguous()
+        for _ in range(6):
+            tsk.contract_iuu(FS, S, h, g, U)
+    else:
+        for _ in range(2):
+            S = tsk.sketch_tensor(T_d, h, g, log2b)
+            tsk.robust_power_method(S, h, g, U0_d, cfg["T"])
+    torch.cuda.synchronize(dev)
+    tsk.check_status(dev)
+    print(f"profile {args.profile} done")
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile", choices=["contract", "build", "rtpm"], default=None)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -348,7 +381,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -158,12 +158,16 @@ int contract_uuu(tsk_ctx* ctx, const float* FS, const float* S, const int32_t* h
  *   lambda_tau = median_m T^(m)(u,u,u); tau* = first argmax; (lambda^, u^) = (lambda_tau*, u_tau*);
  *   deflation: every sketch loses lambda^ * s~_{u^ (x) u^ (x) u^}.
  * Outputs: lambda [k] double, Vout [k][n] float, tau_star [k] int32 (may be NULL),
- * S_deflated: optional [B][b] TSK_C64 receiving the sketches after the k-th deflation.
+ * S_deflated: optional [B][b] TSK_C64 receiving the sketches after the k-th deflation,
+ * lam_all: optional [k][L] float, lambda_tau of every initial vector of every round,
+ * U_iters: optional [k][T][L][n] float, every iterate u_1..u_T of every round (diagnostics;
+ *   lets a caller re-check each power update and selection independently).
  * A zero/non-finite norm in an update is reported by tsk_ctx_status() as TSK_ENONFINITE.
  * Limits: as contract_iuu, 1 <= L <= 4096, T >= 1, k >= 0. */
 int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* h, const uint8_t* g,
                         int B, int log2b, int64_t n, int k, int L, int T, const float* U0,
-                        double* lambda, float* Vout, int32_t* tau_star, float* S_deflated);
+                        double* lambda, float* Vout, int32_t* tau_star, float* S_deflated,
+                        float* lam_all, float* U_iters);
 
 #ifdef __cplusplus
 }

@@ -233,9 +233,10 @@ def contract_uuu(FS: torch.Tensor, S: torch.Tensor, h: torch.Tensor, g: torch.Te
 
 
 def robust_power_method(S: torch.Tensor, h: torch.Tensor, g: torch.Tensor, U0: torch.Tensor,
-                        T: int, return_deflated: bool = False):
+                        T: int, return_deflated: bool = False, return_trace: bool = False):
     """Alg. 1 on B colliding sketches S [B][b] (time domain) with initial vectors U0 [k][L][n].
-    Returns dict(lam [k] float64, V [k][n], tau [k] int32[, S_deflated [B][b]])."""
+    Returns dict(lam [k] float64, V [k][n], tau [k] int32[, S_deflated [B][b]]
+    [, lam_all [k][L], U_iters [k][T][L][n]])."""
     device = S.device
     _need(S, "S", torch.complex64, device)
     B, b = S.shape
@@ -251,13 +252,19 @@ def robust_power_method(S: torch.Tensor, h: torch.Tensor, g: torch.Tensor, U0: t
     V = torch.empty((k, n), dtype=torch.float32, device=device)
     tau = torch.empty((k,), dtype=torch.int32, device=device)
     Sd = torch.empty_like(S) if return_deflated else None
+    lam_all = torch.empty((k, L), dtype=torch.float32, device=device) if return_trace else None
+    U_iters = (torch.empty((k, max(int(T), 0), L, n), dtype=torch.float32, device=device)
+               if return_trace else None)
     rc = _lib.load().robust_power_method(_ctx(device), _ptr(S), _ptr(h), _ptr(g), B, log2b, n, k,
                                          L, int(T), _ptr(U0), _ptr(lam), _ptr(V), _ptr(tau),
-                                         _ptr(Sd))
+                                         _ptr(Sd), _ptr(lam_all), _ptr(U_iters))
     _lib.check("robust_power_method", rc)
     out = {"lam": lam, "V": V, "tau": tau}
     if return_deflated:
         out["S_deflated"] = Sd
+    if return_trace:
+        out["lam_all"] = lam_all
+        out["U_iters"] = U_iters
     return out
 
 

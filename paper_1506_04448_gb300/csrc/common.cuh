@@ -40,10 +40,11 @@ TSK_HD float re_ipow(float2 z, int e) {
   }
 }
 
-// Padded shared-memory index: one float2 of padding after every 32 elements, which spreads
-// the strided stores of the first Stockham pass over more banks.
-TSK_HD int pad_idx(int i) { return i + (i >> 5); }
-TSK_HD constexpr int padded_len(int n) { return n + (n >> 5); }
+// Padded shared-memory index: one float2 of padding after every 16 elements (128 bytes).  A
+// warp's 8-byte accesses are served per half-warp; the first Stockham pass stores element r of
+// butterfly j at 16 j + r, and the padding puts those 16 lanes in 16 different bank pairs.
+TSK_HD int pad_idx(int i) { return i + (i >> 4); }
+TSK_HD constexpr int padded_len(int n) { return n + (n >> 4); }
 
 // ------------------------------------------------------------------ context
 struct tsk_ctx {

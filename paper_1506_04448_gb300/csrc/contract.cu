@@ -142,7 +142,8 @@ extern "C" int contract_uuu(tsk_ctx* ctx, const float* FS, const float* S, const
 extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* h,
                                    const uint8_t* g, int B, int log2b, int64_t n, int k, int L,
                                    int T, const float* U0, double* lambda, float* Vout,
-                                   int32_t* tau_star, float* S_deflated) {
+                                   int32_t* tau_star, float* S_deflated, float* lam_all_out,
+                                   float* U_iters) {
   if (!ctx || !S || !h || !g) return TSK_EINVAL;
   if (k < 0 || T < 0 || B < 1 || L < 1 || n < 1) return TSK_EINVAL;
   if (log2b < 1 || log2b > 24) return TSK_EINVAL;
@@ -206,20 +207,21 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
     for (int t = 0; t < T; ++t) {
       a.U = cur;
       a.normalize_input = (t == 0);
-      a.Unext = bufs[t & 1];
+      a.Unext = U_iters ? U_iters + ((size_t)r * T + t) * L * n : bufs[t & 1];
       a.Vmed = nullptr;
       a.lam_med = nullptr;
       if ((rc = launch_contract(log2b, MODE_IUU, a, st)) != TSK_OK) return rc;
-      cur = bufs[t & 1];
+      cur = a.Unext;
     }
     // selection: lambda_tau = median_m T^(m)(u_tau, u_tau, u_tau)
     a.U = cur;
     a.normalize_input = 0;
     a.Unext = nullptr;
     a.Vmed = nullptr;
-    a.lam_med = lam_med;
+    a.lam_med = lam_all_out ? lam_all_out + (size_t)r * L : lam_med;
     if ((rc = launch_contract(log2b, MODE_UUU, a, st)) != TSK_OK) return rc;
     d.Ucur = cur;
+    d.lam_med = a.lam_med;
     d.round = r;
     if ((rc = launch_deflate(log2b, d, st)) != TSK_OK) return rc;
   }

@@ -51,27 +51,35 @@ TSK_HD float2 mul_w16(float2 z, int e) {
 }
 
 __host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
-__host__ __device__ constexpr int bitrev(int x, int bits) {
-  return bits == 0 ? 0 : ((x & 1) << (bits - 1)) | bitrev(x >> 1, bits - 1);
+// Reverse the low BITS (<= 4) bits of x, without recursion so that it folds after unrolling.
+template <int BITS>
+__host__ __device__ constexpr int bitrev(int x) {
+  static_assert(BITS >= 0 && BITS <= 4, "up to 4 bits");
+  const int r = ((x & 1) << 3) | ((x & 2) << 1) | ((x & 4) >> 1) | ((x & 8) >> 3);
+  return r >> (4 - BITS);
+}
+
+// One radix-2 decimation-in-frequency stage with butterfly distance SPAN, then the next.
+template <int R, int DIR, int SPAN>
+TSK_HD void dif_stage(float2* v) {
+#pragma unroll
+  for (int gbase = 0; gbase < R; gbase += 2 * SPAN) {
+#pragma unroll
+    for (int s = 0; s < SPAN; ++s) {
+      const float2 a = v[gbase + s], c = v[gbase + s + SPAN];
+      v[gbase + s] = cadd(a, c);
+      v[gbase + s + SPAN] = mul_w16<DIR>(csub(a, c), s * (8 / SPAN));
+    }
+  }
+  if constexpr (SPAN > 1) dif_stage<R, DIR, SPAN / 2>(v);
 }
 
 // In-place radix-2 decimation-in-frequency DFT of R <= 16 points held in registers.
-// X_s = sum_r v_r exp(DIR 2 pi i r s / R) ends up in v[bitrev(s, log2 R)].
+// X_s = sum_r v_r exp(DIR 2 pi i r s / R) ends up in v[bitrev<log2 R>(s)].
 template <int R, int DIR>
 TSK_HD void dft_dif(float2* v) {
   static_assert(R == 2 || R == 4 || R == 8 || R == 16, "radix");
-#pragma unroll
-  for (int span = R / 2; span >= 1; span /= 2) {
-#pragma unroll
-    for (int gbase = 0; gbase < R; gbase += 2 * span) {
-#pragma unroll
-      for (int s = 0; s < span; ++s) {
-        const float2 a = v[gbase + s], c = v[gbase + s + span];
-        v[gbase + s] = cadd(a, c);
-        v[gbase + s + span] = mul_w16<DIR>(csub(a, c), s * (8 / span));
-      }
-    }
-  }
+  dif_stage<R, DIR, R / 2>(v);
 }
 
 // exp(DIR * 2 pi i * k / span), span a power of two.
@@ -142,7 +150,7 @@ struct StockhamPass {
       const int k = j & (NS - 1);
       const int base = (j / NS) * NS * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) x[pad_idx(base + r * NS)] = v[q * R + bitrev(r, ilog2(R))];
+      for (int r = 0; r < R; ++r) x[pad_idx(base + r * NS)] = v[q * R + bitrev<ilog2(R)>(r)];
     }
   }
 };
@@ -151,7 +159,8 @@ template <int N, int NT, int NS, int DIR>
 struct FftPasses {
   static constexpr int E = N / NT;
   static constexpr int REM = N / NS;
-  static constexpr int R = REM >= E ? E : REM;
+  static constexpr int RMAX = E > 16 ? 16 : E;
+  static constexpr int R = REM >= RMAX ? RMAX : REM;
   static __device__ __forceinline__ void run(float2* x) {
     float2 v[E];
     StockhamPass<N, NT, R, NS, DIR>::load_compute(x, threadIdx.x, v);
@@ -168,12 +177,12 @@ template <int LOGN, int NT, int DIR>
 __device__ __forceinline__ void block_fft(float2* x) {
   constexpr int N = 1 << LOGN;
   constexpr int E = N / NT;
-  static_assert(E >= 2 && E <= 16 && (E & (E - 1)) == 0, "2..16 elements per thread");
+  static_assert(E >= 2 && E <= 32 && (E & (E - 1)) == 0, "2..32 elements per thread");
   FftPasses<N, NT, 1, DIR>::run(x);
 }
 
-// Threads per block used by the sketch-length-b kernels: b/16 (16 elements per thread for a
-// length-b transform, 8 for a length-b/2 one), at least one warp, at most 1024.
+// Threads per block used by the sketch-length-b kernels: b/16 (one radix-16 butterfly, 16
+// elements, per thread and pass of a length-b transform), at least one warp, at most 1024.
 constexpr int threads_for_logb(int logb) {
   return (1 << logb) / 16 < 32 ? 32 : ((1 << logb) / 16 > 1024 ? 1024 : (1 << logb) / 16);
 }

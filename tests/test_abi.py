@@ -45,7 +45,7 @@ def test_strerror_and_argument_errors_without_gpu(lib):
     assert lib.cs_hashes(None, 1, 1, 10, 1, None, None, None) == -1
     assert lib.contract_iuu(None, None, None, None, None, 1, 10, None, 1, 1, None, None) == -1
     assert lib.robust_power_method(None, None, None, None, 1, 10, 1, 1, 1, 1, None, None, None,
-                                   None, None) == -1
+                                   None, None, None, None) == -1
     assert lib.tsk_ctx_status(None) == -1
 
 
