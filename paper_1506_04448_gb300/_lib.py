@@ -32,6 +32,7 @@ SIGNATURES = {
     "sketch_rank1": (_I, [_P, _I64, _P, _P, _P, _P, _I, _P, _P, _P, _I, _I, _I, _P, _I]),
     "contract_iuu": (_I, [_P, _P, _P, _P, _P, _I, _I, _P, _I, _I64, _P, _P]),
     "contract_uuu": (_I, [_P, _P, _P, _P, _P, _I, _I, _P, _I, _I64, _P, _P]),
+    "contract_iuu_static": (_I, [_P, _P, _P, _P, _I, _I, _P, _I, _I64, _P, _P]),
     "robust_power_method": (_I, [_P, _P, _P, _P, _I, _I, _I64, _I, _I, _I, _P, _P, _P, _P, _P,
                                  _P, _P]),
 }
