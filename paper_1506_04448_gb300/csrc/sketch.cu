@@ -34,11 +34,6 @@ __device__ __forceinline__ void acc_add<long long>(long long* p, long long v) {
   atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
 }
 
-template <typename TIn, typename Acc>
-__device__ __forceinline__ Acc to_acc(TIn x, int kappa) {
-  return (Acc)x * (Acc)kappa;
-}
-
 struct SymSketchArgs {
   const void* T;
   int n;
@@ -51,69 +46,84 @@ struct SymSketchArgs {
 };
 
 template <typename TIn, typename Acc, int PARTS>
-__global__ void __launch_bounds__(1024) sketch_sym_kernel(SymSketchArgs a) {
+__global__ void __launch_bounds__(1024, 1) sketch_sym_kernel(SymSketchArgs a) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
+  __shared__ int s_i0, s_j0;
   const int b = 1 << a.log2b;
   const int n = a.n;
+  const int mask = b - 1;
   const int hist_len = (PARTS == 1 ? 2 : 1) * b;
   Acc* hist = reinterpret_cast<Acc*>(sm_raw);
-  int* hs = reinterpret_cast<int*>(sm_raw + (size_t)hist_len * sizeof(Acc));
-  uint8_t* gs = reinterpret_cast<uint8_t*>(hs + n);
+  // packed hash word q_k = 16 h_k + g_k: in q_i + q_j + q_k, bits 4.. carry h_i + h_j + h_k and
+  // bits 0..3 carry g_i + g_j + g_k (at most 9), so one add gives bucket and sign exponent
+  uint32_t* qs = reinterpret_cast<uint32_t*>(sm_raw + (size_t)hist_len * sizeof(Acc));
   const int m = blockIdx.x / PARTS;
   const int part = blockIdx.x % PARTS;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < hist_len; i += nt) hist[i] = (Acc)0;
-  for (int i = tid; i < n; i += nt) {
-    hs[i] = a.h[(size_t)m * n + i];
-    gs[i] = a.g[(size_t)m * n + i] & 3;
-  }
-  __syncthreads();
+  for (int i = tid; i < n; i += nt)
+    qs[i] = ((uint32_t)(a.h[(size_t)m * n + i] & mask) << 4) | (uint32_t)(a.g[(size_t)m * n + i] & 3);
 
+  // this block owns the wedge rows (i <= j) whose first entry lies in [e0, e1)
   const TIn* T = static_cast<const TIn*>(a.T);
   const long long per_slab = (a.W + a.nslab - 1) / a.nslab;
   const long long e0 = (long long)blockIdx.y * per_slab;
   const long long e1 = min(a.W, e0 + per_slab);
-  const int nw = nt >> 5, w = tid >> 5, lane = tid & 31;
-  const long long per_w = (e1 - e0 + nw - 1) / nw;
-  const long long w0 = e0 + (long long)w * per_w;
-  const long long w1 = min(e1, w0 + per_w);
-  if (w0 < w1) {
-    // first row (i, j) whose start is >= w0
-    int lo = 0, hi = n;  // largest i with wedge_before_i(i) <= w0
+  if (tid == 0) {
+    int lo = 0, hi = n;  // largest i with wedge_before_i(i) <= e0
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (wedge_before_i(n, mid) <= w0) lo = mid; else hi = mid - 1;
+      if (wedge_before_i(n, mid) <= e0) lo = mid; else hi = mid - 1;
     }
-    int i = lo, j;
-    {
-      int jl = i, jh = n;  // smallest j >= i with row_start(i, j) >= w0
-      while (jl < jh) {
-        const int mid = (jl + jh) >> 1;
-        if (wedge_row_start(n, i, mid) >= w0) jh = mid; else jl = mid + 1;
+    int i = lo, jl = lo, jh = n;  // smallest j >= i with row_start(i, j) >= e0
+    while (jl < jh) {
+      const int mid = (jl + jh) >> 1;
+      if (wedge_row_start(n, i, mid) >= e0) jh = mid; else jl = mid + 1;
+    }
+    int j = jl;
+    if (j == n) { ++i; j = i; }
+    s_i0 = i;
+    s_j0 = j;
+  }
+  __syncthreads();
+
+  // rows are dealt to the warps round-robin (neighbouring rows have similar lengths)
+  const int nw = nt >> 5, w = tid >> 5, lane = tid & 31;
+  int i = s_i0, j = s_j0;
+  long long start = (i < n) ? wedge_row_start(n, i, j) : a.W;
+  for (int s = 0; s < w && i < n; ++s) {
+    start += n - j;
+    if (++j == n) { ++i; j = i; }
+  }
+  while (i < n && start < e1) {
+    const TIn* row = T + ((size_t)i * n + j) * (size_t)n;
+    const uint32_t qij = qs[i] + qs[j];
+    const Acc kap_diag = (Acc)((i == j) ? 1 : 3);   // kappa at k == j
+    const Acc kap_off = (Acc)((i == j) ? 3 : 6);    // kappa at k > j
+    constexpr int kU = 4;   // loads in flight per lane before the dependent atomics
+    for (int k0 = j + lane; k0 < n; k0 += 32 * kU) {
+      TIn x[kU];
+#pragma unroll
+      for (int q = 0; q < kU; ++q) {
+        const int k = k0 + 32 * q;
+        x[q] = k < n ? __ldcg(row + k) : (TIn)0;
       }
-      j = jl;
-      if (j == n) { ++i; j = i; }
-    }
-    long long start = (i < n) ? wedge_row_start(n, i, j) : a.W;
-    const int mask = b - 1;
-    while (i < n && start < w1) {
-      const TIn* row = T + ((size_t)i * n + j) * (size_t)n;
-      const int hij = hs[i] + hs[j];
-      const int gij = gs[i] + gs[j];
-      const int kap_diag = (i == j) ? 1 : 3;   // kappa at k == j
-      const int kap_off = (i == j) ? 3 : 6;    // kappa at k > j
-      for (int k = j + lane; k < n; k += 32) {
-        const int kap = (k == j) ? kap_diag : kap_off;
-        Acc v = to_acc<TIn, Acc>(row[k], kap);
-        const int t = (hij + hs[k]) & mask;
-        const int e = (gij + gs[k]) & 3;
-        if (e & 2) v = -v;
+#pragma unroll
+      for (int q = 0; q < kU; ++q) {
+        const int k = k0 + 32 * q;
+        if (k >= n) break;
+        const uint32_t sq = qij + qs[k];
+        Acc v = (Acc)x[q] * (k == j ? kap_diag : kap_off);
+        if (sq & 2) v = -v;
+        const int t = (int)(sq >> 4) & mask;
         if (PARTS == 1) {
-          acc_add<Acc>(&hist[2 * t + (e & 1)], v);
-        } else if ((e & 1) == part) {
+          acc_add<Acc>(&hist[2 * t + (int)(sq & 1)], v);
+        } else if ((int)(sq & 1) == part) {
           acc_add<Acc>(&hist[t], v);
         }
       }
+    }
+    for (int s = 0; s < nw && i < n; ++s) {
       start += n - j;
       if (++j == n) { ++i; j = i; }
     }
@@ -138,7 +148,7 @@ struct AsymSketchArgs {
 };
 
 template <typename TIn, typename Acc>
-__global__ void __launch_bounds__(1024) sketch_asym_kernel(AsymSketchArgs a) {
+__global__ void __launch_bounds__(1024, 1) sketch_asym_kernel(AsymSketchArgs a) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int b = 1 << a.log2b;
   Acc* hist = reinterpret_cast<Acc*>(sm_raw);
@@ -169,10 +179,22 @@ __global__ void __launch_bounds__(1024) sketch_asym_kernel(AsymSketchArgs a) {
     const TIn* row = T + (size_t)r * a.n3;
     const int hij = h1[i] + h2[j];
     const int gij = g1[i] + g2[j];
-    for (int k = lane; k < a.n3; k += 32) {
-      Acc v = (Acc)row[k];
-      if ((gij + g3[k]) & 1) v = -v;
-      acc_add<Acc>(&hist[(hij + h3[k]) & mask], v);
+    constexpr int kU = 4;
+    for (int k0 = lane; k0 < a.n3; k0 += 32 * kU) {
+      TIn x[kU];
+#pragma unroll
+      for (int q = 0; q < kU; ++q) {
+        const int k = k0 + 32 * q;
+        x[q] = k < a.n3 ? __ldcg(row + k) : (TIn)0;
+      }
+#pragma unroll
+      for (int q = 0; q < kU; ++q) {
+        const int k = k0 + 32 * q;
+        if (k >= a.n3) break;
+        Acc v = (Acc)x[q];
+        if ((gij + g3[k]) & 1) v = -v;
+        acc_add<Acc>(&hist[(hij + h3[k]) & mask], v);
+      }
     }
   }
   __syncthreads();
@@ -187,7 +209,7 @@ template <typename TIn, typename Acc, int PARTS>
 static int launch_sym(const SymSketchArgs& a0, int B, tsk_ctx* ctx) {
   SymSketchArgs a = a0;
   const int b = 1 << a.log2b;
-  const size_t smem = (size_t)(PARTS == 1 ? 2 : 1) * b * sizeof(Acc) + (size_t)a.n * 5 + 16;
+  const size_t smem = (size_t)(PARTS == 1 ? 2 : 1) * b * sizeof(Acc) + (size_t)a.n * 4 + 16;
   if (smem > (size_t)ctx->max_smem_optin) return TSK_EUNSUPPORTED;
   TSK_CUDA(cudaFuncSetAttribute(sketch_sym_kernel<TIn, Acc, PARTS>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
