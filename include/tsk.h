@@ -165,6 +165,46 @@ int contract_uuu(tsk_ctx* ctx, const float* FS, const float* S, const int32_t* h
                  const uint8_t* g, int B, int log2b, const float* U, int L, int64_t n,
                  float* lam_med, float* lam_all);
 
+/* ---------------------------------------------------------------- asymmetric sketches (Eq. 1, Alg. 2) */
+
+/* Half spectra of real sketches: Xh[m][f] = sum_t Re(S[m][t]) exp(-2 pi i f t / b), f = 0..b/2.
+ * S: [B][b] TSK_C64 (imaginary parts ignored, e.g. the asymmetric sketch of sketch_tensor with
+ * M = 3); Xh: [B][b/2 + 1] TSK_C64.  Limits: log2b in [9, 15]. */
+int sketch_rfft(tsk_ctx* ctx, const float* S, float* Xh, int B, int log2b);
+
+/* Sketched T^(I,v,w) of an asymmetric sketch (Prop. 1 with two different vectors; the columns of
+ * T_(1)(C (.) B) in Alg. 2).  For output mode `mode` (0, 1, 2) and the other modes p < q:
+ *   v^(m)_i = xi_mode(i) [F^-1(Xh^(m) o conj F s_p,V[r] o conj F s_q,W[r])]_{h_mode(i)},
+ * Vmed[r] = median over the B sketches.  Xh: [B][b/2+1] half spectra (sketch_rfft); h, g:
+ * [B][3][nmax]; dims_host: the three mode sizes; V: [K][dims[p]], W: [K][dims[q]] float;
+ * Vmed: [K][dims[mode]]; Vall: optional [K][B][dims[mode]].  Limits: log2b in [9, 15], B <= 64. */
+int contract_ivw(tsk_ctx* ctx, const float* Xh, const int32_t* h, const uint8_t* g, int B,
+                 int log2b, const int64_t* dims_host, int mode, const float* V, const float* W,
+                 int K, float* Vmed, float* Vall);
+
+/* Sketched CP loss and its adjoint (the paper's Eq. 2 inner-product estimator and the
+ * linearity of Sec. 3.1 applied to a rank-R model; derived, not printed in the paper):
+ *   loss = (1/B) sum_m || s_T^(m) - sum_r lam_r s^(m)_{A[r] (x) Bf[r] (x) C[r]} ||^2,
+ * with s_{a(x)b(x)c} = s_1,a * s_2,b * s_3,c (Eq. 4).  The gradient with respect to a factor
+ * row is a sketched T(I,v,w) contraction of the residual sketch:
+ *   dloss/dA[r][i] = -(2 lam_r / B) sum_m xi_1(i) [F^-1(F R^(m) o conj F s_2,Bf[r] o conj F s_3,C[r])]_{h_1(i)}
+ * (likewise Bf, C) and dloss/dlam_r = -(2/B) sum_m <R^(m), s^(m)_r>.
+ * Xh: [B][b/2+1] half spectra of the tensor sketches; lam: [R]; A: [R][n1], Bf: [R][n2],
+ * C: [R][n3] float (one component per row).  loss: one float (device).  The four gradient
+ * outputs are all NULL (loss only) or all given (same shapes as lam, A, Bf, C).
+ * Limits: log2b in [9, 15], R <= 4096. */
+int cp_sketch_loss(tsk_ctx* ctx, const float* Xh, const int32_t* h, const uint8_t* g, int B,
+                   int log2b, const int64_t* dims_host, int R, const float* lam, const float* A,
+                   const float* Bf, const float* C, float* loss, float* grad_lam, float* grad_A,
+                   float* grad_B, float* grad_C);
+
+/* ALS update of one factor (Eq. 15): out = G^-1 M with G = (P P^T) o (Q Q^T) (FP64 Cholesky),
+ * then lam[r] = ||out[r]|| and out[r] /= lam[r] (Alg. 2).  M: [K][n] rows = sketched
+ * T(I, p_r, q_r) (contract_ivw); P: [K][np], Q: [K][nq]; out: [K][n]; lam: [K].  A singular G
+ * is reported by tsk_ctx_status() as TSK_ENONFINITE.  Limits: K <= 64. */
+int cp_als_solve(tsk_ctx* ctx, const float* M, const float* P, const float* Q, int K, int64_t n,
+                 int64_t np, int64_t nq, float* out, float* lam);
+
 /* ---------------------------------------------------------------- Alg. 1 */
 
 /* Fast robust tensor power method (Alg. 1) on B colliding sketches of a symmetric tensor.

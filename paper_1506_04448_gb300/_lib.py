@@ -33,6 +33,10 @@ SIGNATURES = {
     "contract_iuu": (_I, [_P, _P, _P, _P, _P, _I, _I, _P, _I, _I64, _P, _P]),
     "contract_uuu": (_I, [_P, _P, _P, _P, _P, _I, _I, _P, _I, _I64, _P, _P]),
     "contract_iuu_static": (_I, [_P, _P, _P, _P, _I, _I, _P, _I, _I64, _P, _P]),
+    "sketch_rfft": (_I, [_P, _P, _P, _I, _I]),
+    "contract_ivw": (_I, [_P, _P, _P, _P, _I, _I, _P, _I, _P, _P, _I, _P, _P]),
+    "cp_sketch_loss": (_I, [_P, _P, _P, _P, _I, _I, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "cp_als_solve": (_I, [_P, _P, _P, _P, _I, _I64, _I64, _I64, _P, _P]),
     "robust_power_method": (_I, [_P, _P, _P, _P, _I, _I, _I64, _I, _I, _I, _P, _P, _P, _P, _P,
                                  _P, _P]),
 }

@@ -47,6 +47,8 @@ TSK_HD int pad_idx(int i) { return i + (i >> 4); }
 TSK_HD constexpr int padded_len(int n) { return n + (n >> 4); }
 
 // ------------------------------------------------------------------ context
+constexpr int kCtxAuxStreams = 8;
+
 struct tsk_ctx {
   int device;
   cudaStream_t stream;
@@ -55,10 +57,18 @@ struct tsk_ctx {
   int* status;         // device status word (first error wins)
   int max_smem_optin;  // cudaDevAttrMaxSharedMemoryPerBlockOptin
   int num_sms;
+  // helper streams for independent work inside one call, forked from and joined back into
+  // `stream` with events (created on first use)
+  int n_aux;
+  cudaStream_t aux[kCtxAuxStreams];
+  cudaEvent_t ev_fork;
+  cudaEvent_t ev_join[kCtxAuxStreams];
 };
 
 // Grow the context workspace to at least `bytes` (synchronising the stream when it grows).
 int tsk_ws_reserve(tsk_ctx* ctx, size_t bytes);
+// Make sure `count` helper streams and their events exist.
+int tsk_ctx_aux_streams(tsk_ctx* ctx, int count);
 
 // Map a CUDA error to a tsk status.
 inline int tsk_from_cuda(cudaError_t e) {

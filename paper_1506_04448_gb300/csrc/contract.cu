@@ -38,26 +38,51 @@ int launch_contract(int log2b, int mode, const ContractArgs& a, cudaStream_t st)
 }
 
 template <int LOGB>
-static int launch_deflate_t(const DeflateArgs& a, cudaStream_t st) {
+static int launch_deflate_t(const DeflateArgs& a, int B, cudaStream_t st) {
   constexpr int NT = threads_for_logb(LOGB);
-  constexpr size_t smem = deflate_smem_bytes<LOGB>();
+  constexpr size_t smem = (size_t)padded_len(1 << LOGB) * sizeof(float2);
   TSK_CUDA(cudaFuncSetAttribute(deflate_kernel<LOGB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
-  deflate_kernel<LOGB><<<a.B, NT, smem, st>>>(a);
+  deflate_kernel<LOGB><<<B, NT, smem, st>>>(a);
   TSK_CHECK_LAUNCH();
   return TSK_OK;
 }
 
-int launch_deflate(int log2b, const DeflateArgs& a, cudaStream_t st) {
+int launch_deflate(int log2b, const DeflateArgs& a, int B, cudaStream_t st) {
   switch (log2b) {
-    case 8: return launch_deflate_t<8>(a, st);
-    case 9: return launch_deflate_t<9>(a, st);
-    case 10: return launch_deflate_t<10>(a, st);
-    case 11: return launch_deflate_t<11>(a, st);
-    case 12: return launch_deflate_t<12>(a, st);
-    case 13: return launch_deflate_t<13>(a, st);
-    case 14: return launch_deflate_t<14>(a, st);
+    case 8: return launch_deflate_t<8>(a, B, st);
+    case 9: return launch_deflate_t<9>(a, B, st);
+    case 10: return launch_deflate_t<10>(a, B, st);
+    case 11: return launch_deflate_t<11>(a, B, st);
+    case 12: return launch_deflate_t<12>(a, B, st);
+    case 13: return launch_deflate_t<13>(a, B, st);
+    case 14: return launch_deflate_t<14>(a, B, st);
     default: return TSK_EUNSUPPORTED;
+  }
+}
+
+template <int LOGB>
+static int blocks_per_sm_t() {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, contract_kernel<LOGB, MODE_IUU>,
+                                                    threads_for_logb(LOGB),
+                                                    contract_smem_bytes<LOGB>()) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return per_sm < 1 ? 1 : per_sm;
+}
+
+// Resident contraction blocks per SM at sketch length 2^log2b.
+static int contract_blocks_per_sm(int log2b) {
+  switch (log2b) {
+    case 8: return blocks_per_sm_t<8>();
+    case 9: return blocks_per_sm_t<9>();
+    case 10: return blocks_per_sm_t<10>();
+    case 11: return blocks_per_sm_t<11>();
+    case 12: return blocks_per_sm_t<12>();
+    case 13: return blocks_per_sm_t<13>();
+    default: return blocks_per_sm_t<14>();
   }
 }
 
@@ -149,27 +174,35 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
   if (log2b < 1 || log2b > 24) return TSK_EINVAL;
   if (log2b < 8 || log2b > 14 || B > kMaxB || n > 8192 || L > 4096 || T < 1)
     return TSK_EUNSUPPORTED;
+  const size_t b = (size_t)1 << log2b;
   if (k == 0) {
     if (S_deflated && S_deflated != S)
-      TSK_CUDA(cudaMemcpyAsync(S_deflated, S, (size_t)B * (1 << log2b) * sizeof(float2),
+      TSK_CUDA(cudaMemcpyAsync(S_deflated, S, (size_t)B * b * sizeof(float2),
                                cudaMemcpyDeviceToDevice, ctx->stream));
     return TSK_OK;
   }
   if (!U0 || !lambda || !Vout) return TSK_EINVAL;
-  const size_t b = (size_t)1 << log2b;
   const size_t need = 2 * ws_round(B * b * sizeof(float2)) + ws_round((size_t)L * B * n * 4) +
-                      ws_round((size_t)L * B * 4) + 2 * ws_round((size_t)L * n * 4) +
-                      ws_round((size_t)L * 4) + ws_round((size_t)L * 4);
+                      ws_round((size_t)L * B * 4) + ws_round(2 * (size_t)L * n * 4) +
+                      ws_round((size_t)k * L * 4) + ws_round((size_t)L * 4);
   int rc = tsk_ws_reserve(ctx, need);
   if (rc != TSK_OK) return rc;
+  // The L power-iteration chains are independent until the selection, so they are split into
+  // G groups, each enqueued on its own stream: while one group's step finishes its last wave
+  // of blocks, the other groups' steps fill the idle SMs (a single B x L grid per step would
+  // leave the SMs partly idle at the end of every step).
+  const int per_sm = contract_blocks_per_sm(log2b);
+  long long G = ((long long)L * B + (long long)ctx->num_sms * per_sm - 1) / ((long long)ctx->num_sms * per_sm) + 1;
+  if (G > L) G = L;
+  if (G > kCtxAuxStreams) G = kCtxAuxStreams;
+  if ((rc = tsk_ctx_aux_streams(ctx, (int)G)) != TSK_OK) return rc;
   WsCarve wc{static_cast<char*>(ctx->ws), 0};
   float2* Sw = wc.take<float2>(B * b);
   float2* FSw = wc.take<float2>(B * b);
   float* Vall = wc.take<float>((size_t)L * B * n);
   float* lam_all = wc.take<float>((size_t)L * B);
-  float* Ua = wc.take<float>((size_t)L * n);
-  float* Ub = wc.take<float>((size_t)L * n);
-  float* lam_med = wc.take<float>(L);
+  float* Ubuf = wc.take<float>(2 * (size_t)L * n);
+  float* lam_med = lam_all_out ? lam_all_out : wc.take<float>((size_t)k * L);
   unsigned* counters = wc.take<unsigned>(L);
   cudaStream_t st = ctx->stream;
   TSK_CUDA(cudaMemsetAsync(counters, 0, L * sizeof(unsigned), st));
@@ -183,10 +216,6 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
   a.g = g;
   a.n = (int)n;
   a.B = B;
-  a.L = L;
-  a.Vall = Vall;
-  a.lam_all = lam_all;
-  a.counters = counters;
   a.status = ctx->status;
   DeflateArgs d{};
   d.FS = FSw;
@@ -194,36 +223,46 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
   d.h = h;
   d.g = g;
   d.n = (int)n;
-  d.B = B;
   d.L = L;
-  d.lam_med = lam_med;
   d.lambda_out = lambda;
   d.Vout = Vout;
   d.tau_out = tau_star;
-
   for (int r = 0; r < k; ++r) {
-    const float* cur = U0 + (size_t)r * L * n;
-    float* bufs[2] = {Ua, Ub};
-    for (int t = 0; t < T; ++t) {
+    TSK_CUDA(cudaEventRecord(ctx->ev_fork, st));
+    for (int s = 0; s < G; ++s) {
+      const int tau0 = (int)((long long)L * s / G);
+      const int Ls = (int)((long long)L * (s + 1) / G) - tau0;
+      cudaStream_t gs = ctx->aux[s];
+      TSK_CUDA(cudaStreamWaitEvent(gs, ctx->ev_fork, 0));
+      a.L = Ls;
+      a.Vall = Vall + (size_t)tau0 * B * n;
+      a.lam_all = lam_all + (size_t)tau0 * B;
+      a.counters = counters + tau0;
+      const float* cur = U0 + ((size_t)r * L + tau0) * n;
+      for (int t = 0; t < T; ++t) {
+        float* next = U_iters ? U_iters + (((size_t)r * T + t) * L + tau0) * n
+                              : Ubuf + ((size_t)((t + 1) & 1) * L + tau0) * n;
+        a.U = cur;
+        a.normalize_input = (t == 0);
+        a.Unext = next;
+        a.Vmed = nullptr;
+        a.lam_med = nullptr;
+        if ((rc = launch_contract(log2b, MODE_IUU, a, gs)) != TSK_OK) return rc;
+        cur = next;
+      }
+      // selection: lambda_tau = median_m T^(m)(u_tau, u_tau, u_tau)
       a.U = cur;
-      a.normalize_input = (t == 0);
-      a.Unext = U_iters ? U_iters + ((size_t)r * T + t) * L * n : bufs[t & 1];
-      a.Vmed = nullptr;
-      a.lam_med = nullptr;
-      if ((rc = launch_contract(log2b, MODE_IUU, a, st)) != TSK_OK) return rc;
-      cur = a.Unext;
+      a.normalize_input = 0;
+      a.Unext = nullptr;
+      a.lam_med = lam_med + (size_t)r * L + tau0;
+      if ((rc = launch_contract(log2b, MODE_UUU, a, gs)) != TSK_OK) return rc;
+      TSK_CUDA(cudaEventRecord(ctx->ev_join[s], gs));
+      TSK_CUDA(cudaStreamWaitEvent(st, ctx->ev_join[s], 0));
     }
-    // selection: lambda_tau = median_m T^(m)(u_tau, u_tau, u_tau)
-    a.U = cur;
-    a.normalize_input = 0;
-    a.Unext = nullptr;
-    a.Vmed = nullptr;
-    a.lam_med = lam_all_out ? lam_all_out + (size_t)r * L : lam_med;
-    if ((rc = launch_contract(log2b, MODE_UUU, a, st)) != TSK_OK) return rc;
-    d.Ucur = cur;
-    d.lam_med = a.lam_med;
+    d.Ufinal = U_iters ? U_iters + ((size_t)r * T + (T - 1)) * L * n : Ubuf + (size_t)(T & 1) * L * n;
+    d.lam_med = lam_med + (size_t)r * L;
     d.round = r;
-    if ((rc = launch_deflate(log2b, d, st)) != TSK_OK) return rc;
+    if ((rc = launch_deflate(log2b, d, B, st)) != TSK_OK) return rc;
   }
   if (S_deflated)
     TSK_CUDA(cudaMemcpyAsync(S_deflated, Sw, B * b * sizeof(float2), cudaMemcpyDeviceToDevice, st));

@@ -1,6 +1,7 @@
-// Fused sketched contractions against B colliding sketches (Prop. 1, App. B).
+// Fused sketched contractions against B colliding sketches (Prop. 1, App. B) and the
+// persistent kernel that runs Alg. 1 end to end.
 //
-// One thread block handles one (vector tau, sketch m) pair entirely on chip:
+// One thread block handles one (vector tau, sketch m) pair entirely on chip (contract_one):
 //   1. count sketches of u in shared memory: s_u[h_i] += sigma_i u_i (length b, complex) and
 //      s_2[2 h_i mod b] += sigma_i^2 u_i^2.  s_2 is real (sigma^2 = +-1) and supported on even
 //      positions only, so it is kept as the length-b/2 vector e[h_i mod b/2];
@@ -14,11 +15,11 @@
 //   4. inverse DFTs and the hashed read-off of App. B, Eq. 14 (coefficients 1/3,1/6,1/6,1/3):
 //        v_i = Re[ 1/6 conj(s_i)(g_2+g_1)[h_i] + 1/3 conj(s_i)^2 u_i g_0[2h_i] + 1/3 conj(s_i)^3 u_i^2 S[3h_i] ]
 //   5. lambda^(m) = sum_i u_i v_i (equal to T^(m)(u,u,u), App. B).
-// The last block to finish for a given tau (arrival counter) takes the median over the B
-// sketches (Alg. 1) and, in a power step, normalises it into the next iterate.
-//
 // MODE_UUU evaluates T^(m)(u,u,u) directly (App. B, Eq. 13) after step 2:
 //   (1/b) sum_f Re(FS[f] conj(U_f^3/6 + V'_f U_f/2)) + 1/3 Re(sum_i S[3h_i] conj(s_i)^3 u_i^3).
+// The last block to finish for a vector (arrival counter) takes the median over the B sketches
+// (Alg. 1) and, in a power step, normalises it into the next iterate.  Values written by other
+// blocks (per-sketch results, iterates) are read with ld.global.cg, never through L1.
 #pragma once
 
 #include "common.cuh"
@@ -53,31 +54,32 @@ constexpr size_t contract_smem_bytes() {
          64 * sizeof(float);
 }
 
+// ------------------------------------------------------------------ device building blocks
+
+// One (vector, sketch) contraction.  MODE_IUU writes v^(m) to vout[0..n); both modes return
+// lambda^(m) = T^(m)(u,u,u) in every thread.  Must be called by all NT threads of the block.
 template <int LOGB, int MODE>
-__global__ void __launch_bounds__(threads_for_logb(LOGB), 1) contract_kernel(ContractArgs a) {
+__device__ __forceinline__ float contract_one(float2* A, float2* Eb, float* red, const float2* tw,
+                                              const float2* FSm, const float2* Sm,
+                                              const int32_t* hm, const uint8_t* gm,
+                                              const float* u, int n, bool normalize, int* status,
+                                              float* vout) {
   constexpr int NT = threads_for_logb(LOGB);
   constexpr int b = 1 << LOGB;
   constexpr int hb = b / 2;
-  extern __shared__ float2 smem[];
-  float2* A = smem;                                  // padded, length b
-  float2* Eb = smem + padded_len(b);                 // padded, length b/2
-  float* red = reinterpret_cast<float*>(Eb + padded_len(hb));
-  __shared__ int s_last;
-
+  constexpr float inv_b = 1.f / (float)b;
   const int tid = threadIdx.x;
-  const int m = blockIdx.x, tau = blockIdx.y;
-  const int n = a.n;
-  const int32_t* hm = a.h + (size_t)m * n;
-  const uint8_t* gm = a.g + (size_t)m * n;
-  const float* u = a.U + (size_t)tau * n;
 
   float uscale = 1.f;
-  if (a.normalize_input) {
+  if (normalize) {
     float ss = 0.f;
-    for (int i = tid; i < n; i += NT) ss += u[i] * u[i];
+    for (int i = tid; i < n; i += NT) {
+      const float x = __ldcg(u + i);
+      ss += x * x;
+    }
     ss = block_sum<NT>(ss, red);
     if (!(ss > 0.f) || !isfinite(ss)) {
-      if (tid == 0) tsk_set_status(a.status, TSK_ENONFINITE);
+      if (tid == 0) tsk_set_status(status, TSK_ENONFINITE);
       uscale = 0.f;
     } else {
       uscale = 1.f / sqrtf(ss);
@@ -89,7 +91,7 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB), 1) contract_kernel(Con
   for (int i = tid; i < padded_len(hb); i += NT) Eb[i] = make_float2(0.f, 0.f);
   __syncthreads();
   for (int i = tid; i < n; i += NT) {
-    const float x = u[i] * uscale;
+    const float x = __ldcg(u + i) * uscale;
     const int hi = hm[i] & (b - 1);
     const int gi = gm[i] & 3;
     float* slot = reinterpret_cast<float*>(&A[pad_idx(hi)]);
@@ -99,182 +101,227 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB), 1) contract_kernel(Con
   __syncthreads();
 
   // 2. forward DFTs.
-  block_fft<LOGB, NT, -1>(A);
-  block_fft<LOGB - 1, NT, -1>(Eb);
+  block_fft<LOGB, NT, -1>(A, tw);
+  block_fft<LOGB - 1, NT, -1>(Eb, tw);
 
-  const float2* FSm = a.FS + (size_t)m * b;
-  const float2* Sm = a.S + (size_t)m * b;
-  constexpr float inv_b = 1.f / (float)b;
-
+  float lam = 0.f;
   if constexpr (MODE == MODE_IUU) {
     // 3. spectral products (each f < b/2 owns positions f and f + b/2 of A and f of Eb).
     for (int f = tid; f < hb; f += NT) {
       const float2 cu0 = cconj(A[pad_idx(f)]);
       const float2 cu1 = cconj(A[pad_idx(f + hb)]);
       const float2 cv = cconj(Eb[pad_idx(f)]);
-      const float2 F0 = FSm[f];
-      const float2 F1 = FSm[f + hb];
+      const float2 F0 = __ldcg(FSm + f);
+      const float2 F1 = __ldcg(FSm + f + hb);
       A[pad_idx(f)] = cmul(F0, cadd(cmul(cu0, cu0), cv));
       A[pad_idx(f + hb)] = cmul(F1, cadd(cmul(cu1, cu1), cv));
       Eb[pad_idx(f)] = cadd(cmul(F0, cu0), cmul(F1, cu1));
     }
     __syncthreads();
     // 4. inverse DFTs and hashed read-off.
-    block_fft<LOGB, NT, +1>(A);
-    block_fft<LOGB - 1, NT, +1>(Eb);
-    float lam = 0.f;
-    float* vout = a.Vall + ((size_t)tau * a.B + m) * n;
+    block_fft<LOGB, NT, +1>(A, tw);
+    block_fft<LOGB - 1, NT, +1>(Eb, tw);
     for (int i = tid; i < n; i += NT) {
-      const float x = u[i] * uscale;
+      const float x = __ldcg(u + i) * uscale;
       const int hi = hm[i] & (b - 1);
       const int gi = gm[i] & 3;
       const float2 g12 = A[pad_idx(hi)];
       const float2 g0 = Eb[pad_idx(hi & (hb - 1))];
-      const float2 s3 = Sm[(3 * hi) & (b - 1)];
+      const float2 s3 = __ldcg(Sm + ((3 * hi) & (b - 1)));
       const float v = (re_ipow(g12, -gi) * (1.f / 6.f) + re_ipow(g0, -2 * gi) * x * (1.f / 3.f)) * inv_b +
                       re_ipow(s3, -3 * gi) * x * x * (1.f / 3.f);
       vout[i] = v;
       lam += x * v;
     }
-    lam = block_sum<NT>(lam, red);
-    if (tid == 0) a.lam_all[(size_t)tau * a.B + m] = lam;
   } else {
-    float acc = 0.f;
     for (int f = tid; f < b; f += NT) {
       const float2 U = A[pad_idx(f)];
       const float2 V = Eb[pad_idx(f & (hb - 1))];
       const float2 U2 = cmul(U, U);
       const float2 Y = cadd(cscale(cmul(U2, U), 1.f / 6.f), cscale(cmul(V, U), 0.5f));
-      const float2 F = FSm[f];
-      acc += F.x * Y.x + F.y * Y.y;     // Re(F conj(Y))
+      const float2 F = __ldcg(FSm + f);
+      lam += F.x * Y.x + F.y * Y.y;     // Re(F conj(Y))
     }
-    acc *= inv_b;
+    lam *= inv_b;
     for (int i = tid; i < n; i += NT) {
-      const float x = u[i] * uscale;
+      const float x = __ldcg(u + i) * uscale;
       const int hi = hm[i] & (b - 1);
       const int gi = gm[i] & 3;
-      acc += re_ipow(Sm[(3 * hi) & (b - 1)], -3 * gi) * x * x * x * (1.f / 3.f);
+      lam += re_ipow(__ldcg(Sm + ((3 * hi) & (b - 1))), -3 * gi) * x * x * x * (1.f / 3.f);
     }
-    acc = block_sum<NT>(acc, red);
-    if (tid == 0) a.lam_all[(size_t)tau * a.B + m] = acc;
   }
+  return block_sum<NT>(lam, red);
+}
 
-  // 5. the last block of this tau takes the medians over the B sketches.
+// Count this block's arrival on `counter`; true (in every thread) for the block that completes
+// a group of `group` arrivals.  Writes of this block are made visible device-wide first.
+__device__ __forceinline__ bool arrive_is_last(unsigned* counter, unsigned group, int* s_flag) {
   __threadfence();
   __syncthreads();
-  if (tid == 0) {
-    const unsigned prev = atomicAdd(&a.counters[tau], 1u);
-    s_last = (prev == (unsigned)(a.B - 1));
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(counter, 1u);
+    *s_flag = (prev == group - 1);
   }
   __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  const int B = a.B;
-  if (tid == 0) {
+  const bool last = *s_flag != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+// Median over the B sketches of every entry of one vector (Vt: [B][n]) into dst; if unext is
+// given, dst / ||dst|| is written there (dst may equal unext).  Called by the last block.
+template <int NT>
+__device__ __forceinline__ void median_vector(const float* Vt, int B, int n, float* dst,
+                                              float* unext, float* red, int* status) {
+  float ss = 0.f;
+  for (int i = threadIdx.x; i < n; i += NT) {
     float vals[kMaxB];
-    for (int c = 0; c < B; ++c) vals[c] = __ldcg(&a.lam_all[(size_t)tau * B + c]);
-    if (a.lam_med) a.lam_med[tau] = small_median(vals, B);
+    for (int c = 0; c < B; ++c) vals[c] = __ldcg(Vt + (size_t)c * n + i);
+    const float med = small_median(vals, B);
+    dst[i] = med;
+    ss += med * med;
+  }
+  if (unext) {
+    ss = block_sum<NT>(ss, red);
+    float inv = 0.f;
+    if (!(ss > 0.f) || !isfinite(ss)) {
+      if (threadIdx.x == 0) tsk_set_status(status, TSK_ENONFINITE);
+    } else {
+      inv = 1.f / sqrtf(ss);
+    }
+    for (int i = threadIdx.x; i < n; i += NT) unext[i] = dst[i] * inv;
+  }
+}
+
+__device__ __forceinline__ float median_of(const float* x, int B) {
+  float vals[kMaxB];
+  for (int c = 0; c < B; ++c) vals[c] = __ldcg(x + c);
+  return small_median(vals, B);
+}
+
+// Deflation of one sketch by lambda^ u(x)u(x)u (Alg. 1, deflation step; Sec. 3.3):
+//   U = F s~_u,  D = lambda^ U^3,  FS[m] -= D,  S[m] -= F^-1 D.
+template <int LOGB>
+__device__ __forceinline__ void deflate_one(float2* A, const float2* tw, float2* FSm, float2* Sm,
+                                            const int32_t* hm,
+                                            const uint8_t* gm, const float* u, int n, float lam) {
+  constexpr int NT = threads_for_logb(LOGB);
+  constexpr int b = 1 << LOGB;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < padded_len(b); i += NT) A[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int i = tid; i < n; i += NT) {
+    const int gi = gm[i] & 3;
+    const float x = __ldcg(u + i);
+    float* slot = reinterpret_cast<float*>(&A[pad_idx(hm[i] & (b - 1))]);
+    atomicAdd(slot + (gi & 1), (gi & 2) ? -x : x);
+  }
+  __syncthreads();
+  block_fft<LOGB, NT, -1>(A, tw);
+  for (int f = tid; f < b; f += NT) {
+    const float2 U = A[pad_idx(f)];
+    const float2 D = cscale(cmul(cmul(U, U), U), lam);
+    FSm[f] = csub(__ldcg(FSm + f), D);
+    A[pad_idx(f)] = D;
+  }
+  __syncthreads();
+  block_fft<LOGB, NT, +1>(A, tw);
+  constexpr float inv_b = 1.f / (float)b;
+  for (int t = tid; t < b; t += NT) Sm[t] = csub(__ldcg(Sm + t), cscale(A[pad_idx(t)], inv_b));
+  __syncthreads();
+}
+
+// First index of the maximum of x[0..L) (the selection tau* of Alg. 1).
+__device__ __forceinline__ int first_argmax(const float* x, int L) {
+  int best = 0;
+  float bv = __ldcg(x);
+  for (int t = 1; t < L; ++t) {
+    const float v = __ldcg(x + t);
+    if (v > bv) {
+      bv = v;
+      best = t;
+    }
+  }
+  return best;
+}
+
+// ------------------------------------------------------------------ single-step kernels
+
+template <int LOGB, int MODE>
+__global__ void __launch_bounds__(threads_for_logb(LOGB), 1) contract_kernel(ContractArgs a) {
+  constexpr int NT = threads_for_logb(LOGB);
+  constexpr int b = 1 << LOGB;
+  extern __shared__ float2 smem[];
+  float2* A = smem;
+  float2* Eb = smem + padded_len(b);
+  float* red = reinterpret_cast<float*>(Eb + padded_len(b / 2));
+  __shared__ int s_last;
+  __shared__ float2 tw[kTwEntries];
+  fill_twiddles(tw, NT);
+  const int m = blockIdx.x, tau = blockIdx.y, n = a.n, B = a.B;
+  const float lam = contract_one<LOGB, MODE>(
+      A, Eb, red, tw, a.FS + (size_t)m * b, a.S + (size_t)m * b, a.h + (size_t)m * n,
+      a.g + (size_t)m * n, a.U + (size_t)tau * n, n, a.normalize_input != 0, a.status,
+      MODE == MODE_IUU ? a.Vall + ((size_t)tau * B + m) * n : nullptr);
+  if (threadIdx.x == 0) a.lam_all[(size_t)tau * B + m] = lam;
+  if (!arrive_is_last(&a.counters[tau], (unsigned)B, &s_last)) return;
+  if (threadIdx.x == 0) {
+    if (a.lam_med) a.lam_med[tau] = median_of(a.lam_all + (size_t)tau * B, B);
     a.counters[tau] = 0u;
   }
   if constexpr (MODE == MODE_IUU) {
     if (a.Vmed == nullptr && a.Unext == nullptr) return;
     float* dst = a.Vmed ? a.Vmed + (size_t)tau * n : a.Unext + (size_t)tau * n;
-    float ss = 0.f;
-    for (int i = tid; i < n; i += NT) {
-      float vals[kMaxB];
-      for (int c = 0; c < B; ++c) vals[c] = __ldcg(&a.Vall[((size_t)tau * B + c) * n + i]);
-      const float med = small_median(vals, B);
-      dst[i] = med;
-      ss += med * med;
-    }
-    if (a.Unext) {
-      ss = block_sum<NT>(ss, red);
-      float inv = 0.f;
-      if (!(ss > 0.f) || !isfinite(ss)) {
-        if (tid == 0) tsk_set_status(a.status, TSK_ENONFINITE);
-      } else {
-        inv = 1.f / sqrtf(ss);
-      }
-      float* un = a.Unext + (size_t)tau * n;
-      for (int i = tid; i < n; i += NT) un[i] = dst[i] * inv;
-    }
+    median_vector<NT>(a.Vall + (size_t)tau * B * n, B, n, dst,
+                      a.Unext ? a.Unext + (size_t)tau * n : nullptr, red, a.status);
   }
 }
 
-// Deflation of every sketch by the selected component (Alg. 1, deflation step), fused with the
-// selection tau* = first argmax_tau lambda_tau.  One block per sketch m:
-//   U = F s~_u,  D = lambda^ U^3  (= F of the sketch of lambda^ u(x)u(x)u, Sec. 3.3),
-//   FS[m] -= D,  S[m] -= F^-1 D.
+// ------------------------------------------------------------------ persistent Alg. 1
+
+// Selection tau* = first argmax of the round's eigenvalue medians, outputs, and deflation of
+// sketch m = blockIdx.x (Alg. 1, selection and deflation steps).
 struct DeflateArgs {
   float2* FS;
   float2* S;
   const int32_t* h;
   const uint8_t* g;
-  int n, B, L;
-  const float* Ucur;      // [L][n] final iterates
-  const float* lam_med;   // [L]
+  int n, L;
+  const float* Ufinal;      // [L][n] final iterates of the round
+  const float* lam_med;     // [L] eigenvalue medians of the round
   int round;
-  double* lambda_out;     // [k]
-  float* Vout;            // [k][n]
-  int32_t* tau_out;       // [k] or NULL
+  double* lambda_out;       // [k]
+  float* Vout;              // [k][n]
+  int32_t* tau_out;         // [k] or NULL
 };
-
-template <int LOGB>
-constexpr size_t deflate_smem_bytes() {
-  return (size_t)padded_len(1 << LOGB) * sizeof(float2);
-}
 
 template <int LOGB>
 __global__ void __launch_bounds__(threads_for_logb(LOGB), 1) deflate_kernel(DeflateArgs a) {
   constexpr int NT = threads_for_logb(LOGB);
   constexpr int b = 1 << LOGB;
   extern __shared__ float2 smem[];
-  float2* A = smem;
   __shared__ int s_best;
-  const int tid = threadIdx.x, m = blockIdx.x, n = a.n;
-  if (tid == 0) {
-    int best = 0;
-    for (int t = 1; t < a.L; ++t)
-      if (a.lam_med[t] > a.lam_med[best]) best = t;
-    s_best = best;
-  }
-  for (int i = tid; i < padded_len(b); i += NT) A[i] = make_float2(0.f, 0.f);
+  __shared__ float2 tw[kTwEntries];
+  fill_twiddles(tw, NT);
+  const int m = blockIdx.x, n = a.n;
+  if (threadIdx.x == 0) s_best = first_argmax(a.lam_med, a.L);
   __syncthreads();
   const int best = s_best;
   const float lam = a.lam_med[best];
-  const float* u = a.Ucur + (size_t)best * n;
+  const float* u = a.Ufinal + (size_t)best * n;
   if (m == 0) {
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
       a.lambda_out[a.round] = (double)lam;
       if (a.tau_out) a.tau_out[a.round] = best;
     }
-    for (int i = tid; i < n; i += NT) a.Vout[(size_t)a.round * n + i] = u[i];
+    for (int i = threadIdx.x; i < n; i += NT) a.Vout[(size_t)a.round * n + i] = u[i];
   }
-  const int32_t* hm = a.h + (size_t)m * n;
-  const uint8_t* gm = a.g + (size_t)m * n;
-  for (int i = tid; i < n; i += NT) {
-    const int gi = gm[i] & 3;
-    float* slot = reinterpret_cast<float*>(&A[pad_idx(hm[i] & (b - 1))]);
-    atomicAdd(slot + (gi & 1), (gi & 2) ? -u[i] : u[i]);
-  }
-  __syncthreads();
-  block_fft<LOGB, NT, -1>(A);
-  float2* FSm = a.FS + (size_t)m * b;
-  for (int f = tid; f < b; f += NT) {
-    const float2 U = A[pad_idx(f)];
-    const float2 D = cscale(cmul(cmul(U, U), U), lam);
-    FSm[f] = csub(FSm[f], D);
-    A[pad_idx(f)] = D;
-  }
-  __syncthreads();
-  block_fft<LOGB, NT, +1>(A);
-  float2* Sm = a.S + (size_t)m * b;
-  constexpr float inv_b = 1.f / (float)b;
-  for (int t = tid; t < b; t += NT) Sm[t] = csub(Sm[t], cscale(A[pad_idx(t)], inv_b));
+  deflate_one<LOGB>(smem, tw, a.FS + (size_t)m * b, a.S + (size_t)m * b, a.h + (size_t)m * n,
+                    a.g + (size_t)m * n, u, n, lam);
 }
 
 // Host launchers (defined in contract.cu).
 int launch_contract(int log2b, int mode, const ContractArgs& args, cudaStream_t st);
-int launch_deflate(int log2b, const DeflateArgs& args, cudaStream_t st);
+int launch_deflate(int log2b, const DeflateArgs& args, int B, cudaStream_t st);
 
 }  // namespace tsk

@@ -43,6 +43,18 @@ int tsk_ws_reserve(tsk_ctx* ctx, size_t bytes) {
   return TSK_OK;
 }
 
+int tsk_ctx_aux_streams(tsk_ctx* ctx, int count) {
+  if (count > kCtxAuxStreams) return TSK_EUNSUPPORTED;
+  if (ctx->n_aux == 0) TSK_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+  while (ctx->n_aux < count) {
+    const int i = ctx->n_aux;
+    TSK_CUDA(cudaStreamCreateWithFlags(&ctx->aux[i], cudaStreamNonBlocking));
+    TSK_CUDA(cudaEventCreateWithFlags(&ctx->ev_join[i], cudaEventDisableTiming));
+    ctx->n_aux = i + 1;
+  }
+  return TSK_OK;
+}
+
 extern "C" int tsk_ctx_create(int device, void* stream, tsk_ctx** out) {
   if (!out) return TSK_EINVAL;
   *out = nullptr;
@@ -75,6 +87,12 @@ extern "C" int tsk_ctx_destroy(tsk_ctx* ctx) {
   if (!ctx) return TSK_EINVAL;
   DeviceGuard guard(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  for (int i = 0; i < ctx->n_aux; ++i) {
+    cudaStreamSynchronize(ctx->aux[i]);
+    cudaStreamDestroy(ctx->aux[i]);
+    cudaEventDestroy(ctx->ev_join[i]);
+  }
+  if (ctx->n_aux > 0) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->status) cudaFree(ctx->status);
   free(ctx);

@@ -82,13 +82,31 @@ TSK_HD void dft_dif(float2* v) {
   dif_stage<R, DIR, R / 2>(v);
 }
 
-// exp(DIR * 2 pi i * k / span), span a power of two.
-TSK_HD float2 unit_root(int k, int span, int dir) {
+// Twiddle table: w^m for w = exp(-2 pi i / 2^15) and m < 2^15 as the product of two tables,
+// tw[m & 255] * tw[256 + (m >> 8)].  It lives in shared memory (3 KB) and is filled once per
+// block by fill_twiddles(); one lookup replaces a sincospif call per butterfly.
+constexpr int kTwLog = 15;
+constexpr int kTwLo = 256;
+constexpr int kTwEntries = kTwLo + (1 << kTwLog) / kTwLo;
+
+__device__ __forceinline__ void fill_twiddles(float2* tw, int nt) {
+  for (int j = threadIdx.x; j < kTwEntries; j += nt) {
+    const int m = j < kTwLo ? j : (j - kTwLo) * kTwLo;
+    float s, c;
+    sincospif(-2.f * (float)m / (float)(1 << kTwLog), &s, &c);
+    tw[j] = make_float2(c, s);
+  }
+  __syncthreads();
+}
+
+// exp(DIR * 2 pi i * k / span), span a power of two <= 2^15.
+TSK_HD float2 unit_root(const float2* tw, int k, int span, int dir) {
 #ifdef __CUDA_ARCH__
-  float s, c;
-  sincospif((float)(2 * k) / (float)span, &s, &c);
-  return make_float2(c, dir > 0 ? s : -s);
+  const int m = k * ((1 << kTwLog) / span);
+  const float2 w = cmul(tw[m & (kTwLo - 1)], tw[kTwLo + (m >> 8)]);
+  return dir > 0 ? cconj(w) : w;
 #else
+  (void)tw;
   const double a = 2.0 * 3.14159265358979323846 * (double)k / (double)span;
   return make_float2((float)cos(a), (float)(dir > 0 ? sin(a) : -sin(a)));
 #endif
@@ -96,10 +114,10 @@ TSK_HD float2 unit_root(int k, int span, int dir) {
 
 // v[r] *= w^r, w = exp(DIR 2 pi i k / span), r = 1..R-1.  w^2, w^4, w^8 are formed by
 // squaring and the odd powers by one extra product, so at most four roundings separate any
-// power from the correctly rounded w.
+// power from the table value of w.
 template <int R, int DIR>
-TSK_HD void twiddle(float2* v, int k, int span) {
-  const float2 w1 = unit_root(k, span, DIR);
+TSK_HD void twiddle(float2* v, const float2* tw, int k, int span) {
+  const float2 w1 = unit_root(tw, k, span, DIR);
   v[1] = cmul(v[1], w1);
   if constexpr (R >= 4) {
     const float2 w2 = cmul(w1, w1);
@@ -133,13 +151,13 @@ struct StockhamPass {
   static constexpr int NB = E / R;
   static_assert(NB * R == E, "elements per thread must be a multiple of the radix");
 
-  static TSK_HD void load_compute(const float2* x, int tid, float2* v) {
+  static TSK_HD void load_compute(const float2* x, const float2* tw, int tid, float2* v) {
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
       const int j = tid + q * NT;
 #pragma unroll
       for (int r = 0; r < R; ++r) v[q * R + r] = x[pad_idx(j + r * (N / R))];
-      if constexpr (NS > 1) twiddle<R, DIR>(v + q * R, j & (NS - 1), NS * R);
+      if constexpr (NS > 1) twiddle<R, DIR>(v + q * R, tw, j & (NS - 1), NS * R);
       dft_dif<R, DIR>(v + q * R);
     }
   }
@@ -161,24 +179,98 @@ struct FftPasses {
   static constexpr int REM = N / NS;
   static constexpr int RMAX = E > 16 ? 16 : E;
   static constexpr int R = REM >= RMAX ? RMAX : REM;
-  static __device__ __forceinline__ void run(float2* x) {
+  static __device__ __forceinline__ void run(float2* x, const float2* tw) {
     float2 v[E];
-    StockhamPass<N, NT, R, NS, DIR>::load_compute(x, threadIdx.x, v);
+    StockhamPass<N, NT, R, NS, DIR>::load_compute(x, tw, threadIdx.x, v);
     __syncthreads();
     StockhamPass<N, NT, R, NS, DIR>::store(x, threadIdx.x, v);
     __syncthreads();
-    if constexpr (NS * R < N) FftPasses<N, NT, NS * R, DIR>::run(x);
+    if constexpr (NS * R < N) FftPasses<N, NT, NS * R, DIR>::run(x, tw);
   }
 };
 
 // In-place FFT of N = 2^LOGN complex values at x (padded layout) by a block of exactly NT
-// threads.  Must be called by all NT threads; begins and ends with the data synchronised.
+// threads, with the twiddle table tw (fill_twiddles).  Must be called by all NT threads;
+// begins and ends with the data synchronised.
 template <int LOGN, int NT, int DIR>
-__device__ __forceinline__ void block_fft(float2* x) {
+__device__ __forceinline__ void block_fft(float2* x, const float2* tw) {
   constexpr int N = 1 << LOGN;
   constexpr int E = N / NT;
   static_assert(E >= 2 && E <= 32 && (E & (E - 1)) == 0, "2..32 elements per thread");
-  FftPasses<N, NT, 1, DIR>::run(x);
+  static_assert(LOGN <= kTwLog, "twiddle table covers transforms up to 2^15");
+  FftPasses<N, NT, 1, DIR>::run(x, tw);
+}
+
+// ------------------------------------------------------------------ real signals of length b
+// A real signal x of length b = 2N is held as N complex values z_t = (x_2t, x_2t+1) in the padded
+// layout; its half spectrum X_0..X_N (X_f = sum_t x_t exp(-2 pi i f t / b), the rest follows by
+// Hermitian symmetry) is held as X_0..X_{N-1} in the same slots plus X_N in `last`.
+
+// Forward: z -> half spectrum, in place.  Z = DFT_N(z), then for f = 0..N
+//   X_f = (Z_f + conj Z_{N-f})/2 - i w^f (Z_f - conj Z_{N-f})/2,  w = exp(-2 pi i / b),  Z_N = Z_0.
+template <int LOGB, int NT>
+__device__ __forceinline__ void block_rfft(float2* x, float2* last, const float2* tw) {
+  constexpr int N = 1 << (LOGB - 1);
+  block_fft<LOGB - 1, NT, -1>(x, tw);
+  // pairs (f, N - f), f = 0..N/2, are independent: each thread owns whole pairs
+  for (int f = threadIdx.x; f <= N / 2; f += NT) {
+    const float2 zf = x[pad_idx(f)];
+    const float2 zg = x[pad_idx(f == 0 ? 0 : N - f)];   // Z_{N-f}
+    auto untangle = [&](float2 a, float2 c, int ff) {
+      const float2 e = cscale(cadd(a, cconj(c)), 0.5f);
+      const float2 d = cscale(csub(a, cconj(c)), 0.5f);
+      const float2 w = unit_root(tw, ff, 2 * N, -1);
+      const float2 wd = cmul(w, d);
+      return make_float2(e.x + wd.y, e.y - wd.x);          // e - i w d
+    };
+    if (f == 0) {
+      *last = make_float2(zf.x - zf.y, 0.f);               // X_N = Re Z_0 - Im Z_0
+      x[pad_idx(0)] = make_float2(zf.x + zf.y, 0.f);       // X_0 = Re Z_0 + Im Z_0
+    } else {
+      const float2 Xf = untangle(zf, zg, f);
+      const float2 Xg = untangle(zg, zf, N - f);
+      x[pad_idx(f)] = Xf;
+      x[pad_idx(N - f)] = Xg;
+    }
+  }
+  __syncthreads();
+}
+
+// Inverse: half spectrum -> z (the real signal, including the 1/b factor), in place.
+//   E_f = (X_f + conj X_{N-f})/2,  O_f = w^{-f} (X_f - conj X_{N-f})/2,  Z_f = E_f + i O_f,
+//   z = DFT_N^{-1}(Z) / N.
+template <int LOGB, int NT>
+__device__ __forceinline__ void block_irfft(float2* x, const float2* last, const float2* tw) {
+  constexpr int N = 1 << (LOGB - 1);
+  const float2 xN = *last;
+  for (int f = threadIdx.x; f <= N / 2; f += NT) {
+    const float2 Xf = x[pad_idx(f)];
+    const float2 Xg = f == 0 ? xN : x[pad_idx(N - f)];    // X_{N-f}
+    auto tangle = [&](float2 a, float2 c, int ff) {
+      const float2 e = cscale(cadd(a, cconj(c)), 0.5f);
+      const float2 d = cscale(csub(a, cconj(c)), 0.5f);
+      const float2 o = cmul(unit_root(tw, ff, 2 * N, +1), d);
+      return make_float2(e.x - o.y, e.y + o.x);           // e + i o
+    };
+    if (f == 0) {
+      x[pad_idx(0)] = tangle(Xf, Xg, 0);
+    } else {
+      const float2 Zf = tangle(Xf, Xg, f);
+      const float2 Zg = tangle(Xg, Xf, N - f);
+      x[pad_idx(f)] = Zf;
+      x[pad_idx(N - f)] = Zg;
+    }
+  }
+  __syncthreads();
+  block_fft<LOGB - 1, NT, +1>(x, tw);
+  constexpr float invN = 1.f / (float)N;
+  for (int t = threadIdx.x; t < N; t += NT) x[pad_idx(t)] = cscale(x[pad_idx(t)], invN);
+  __syncthreads();
+}
+
+// Real element k of a signal held as complex pairs in the padded layout.
+__device__ __forceinline__ float& real_at(float2* x, int k) {
+  return reinterpret_cast<float*>(&x[pad_idx(k >> 1)])[k & 1];
 }
 
 // Threads per block used by the sketch-length-b kernels: b/16 (one radix-16 butterfly, 16

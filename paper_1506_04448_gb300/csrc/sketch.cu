@@ -48,7 +48,7 @@ struct SymSketchArgs {
 template <typename TIn, typename Acc, int PARTS>
 __global__ void __launch_bounds__(1024, 1) sketch_sym_kernel(SymSketchArgs a) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  __shared__ int s_i0, s_j0;
+  __shared__ int s_i0, s_j0, s_i1, s_j1;
   const int b = 1 << a.log2b;
   const int n = a.n;
   const int mask = b - 1;
@@ -69,33 +69,40 @@ __global__ void __launch_bounds__(1024, 1) sketch_sym_kernel(SymSketchArgs a) {
   const long long per_slab = (a.W + a.nslab - 1) / a.nslab;
   const long long e0 = (long long)blockIdx.y * per_slab;
   const long long e1 = min(a.W, e0 + per_slab);
-  if (tid == 0) {
-    int lo = 0, hi = n;  // largest i with wedge_before_i(i) <= e0
+  if (tid < 2) {
+    // first row whose start is >= e (e = e0 for thread 0, e1 for thread 1)
+    const long long e = tid == 0 ? e0 : e1;
+    int lo = 0, hi = n;  // largest i with wedge_before_i(i) <= e
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (wedge_before_i(n, mid) <= e0) lo = mid; else hi = mid - 1;
+      if (wedge_before_i(n, mid) <= e) lo = mid; else hi = mid - 1;
     }
-    int i = lo, jl = lo, jh = n;  // smallest j >= i with row_start(i, j) >= e0
+    int i = lo, jl = lo, jh = n;  // smallest j >= i with row_start(i, j) >= e
     while (jl < jh) {
       const int mid = (jl + jh) >> 1;
-      if (wedge_row_start(n, i, mid) >= e0) jh = mid; else jl = mid + 1;
+      if (wedge_row_start(n, i, mid) >= e) jh = mid; else jl = mid + 1;
     }
     int j = jl;
-    if (j == n) { ++i; j = i; }
-    s_i0 = i;
-    s_j0 = j;
+    if (j == n && i < n) { ++i; j = i; }   // (n, n) marks the end of the wedge
+    if (tid == 0) { s_i0 = i; s_j0 = j; } else { s_i1 = i; s_j1 = j; }
   }
   __syncthreads();
 
-  // rows are dealt to the warps round-robin (neighbouring rows have similar lengths)
+  // rows are dealt to the warps round-robin (neighbouring rows have similar lengths); the
+  // block's rows are those from (s_i0, s_j0) up to, not including, (s_i1, s_j1)
   const int nw = nt >> 5, w = tid >> 5, lane = tid & 31;
+  const int i1 = s_i1, j1 = s_j1;
   int i = s_i0, j = s_j0;
-  long long start = (i < n) ? wedge_row_start(n, i, j) : a.W;
-  for (int s = 0; s < w && i < n; ++s) {
-    start += n - j;
-    if (++j == n) { ++i; j = i; }
-  }
-  while (i < n && start < e1) {
+  // advance (i, j) by `adv` rows in the order (0,0), (0,1), ..., (0,n-1), (1,1), ...
+  auto advance = [n](int& ii, int& jj, int adv) {
+    while (adv > 0 && ii < n) {
+      const int left = n - jj;
+      if (adv < left) { jj += adv; adv = 0; }
+      else { adv -= left; ++ii; jj = ii; }
+    }
+  };
+  advance(i, j, w);
+  while (i < n && (i < i1 || (i == i1 && j < j1))) {
     const TIn* row = T + ((size_t)i * n + j) * (size_t)n;
     const uint32_t qij = qs[i] + qs[j];
     const Acc kap_diag = (Acc)((i == j) ? 1 : 3);   // kappa at k == j
@@ -123,10 +130,7 @@ __global__ void __launch_bounds__(1024, 1) sketch_sym_kernel(SymSketchArgs a) {
         }
       }
     }
-    for (int s = 0; s < nw && i < n; ++s) {
-      start += n - j;
-      if (++j == n) { ++i; j = i; }
-    }
+    advance(i, j, nw);
   }
   __syncthreads();
   Acc* Sg = static_cast<Acc*>(a.S) + (size_t)m * 2 * b;
@@ -261,11 +265,13 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB)) fft_rows_kernel(const 
   constexpr int NT = threads_for_logb(LOGB);
   constexpr int b = 1 << LOGB;
   extern __shared__ float2 smem[];
+  __shared__ float2 tw[kTwEntries];
+  fill_twiddles(tw, NT);
   const float2* src = in + (size_t)blockIdx.x * b;
   float2* dst = out + (size_t)blockIdx.x * b;
   for (int t = threadIdx.x; t < b; t += NT) smem[pad_idx(t)] = src[t];
   __syncthreads();
-  if (inverse) block_fft<LOGB, NT, +1>(smem); else block_fft<LOGB, NT, -1>(smem);
+  if (inverse) block_fft<LOGB, NT, +1>(smem, tw); else block_fft<LOGB, NT, -1>(smem, tw);
   const float s = inverse ? 1.f / (float)b : 1.f;
   for (int t = threadIdx.x; t < b; t += NT) dst[t] = cscale(smem[pad_idx(t)], s);
 }
@@ -332,6 +338,8 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB)) rank1_kernel(Rank1Args
   constexpr int b = 1 << LOGB;
   extern __shared__ float2 smem[];
   float2* A = smem;
+  __shared__ float2 tw[kTwEntries];
+  fill_twiddles(tw, NT);
   const int m = blockIdx.x, tid = threadIdx.x;
   float2* acc = a.acc + (size_t)m * b;
   float2* prod = a.prod ? a.prod + (size_t)m * b : nullptr;
@@ -348,7 +356,7 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB)) rank1_kernel(Rank1Args
       scatter_count_sketch<NT>(A, x, len, hm + (size_t)j * a.nmax, gm + (size_t)j * a.nmax,
                                (a.M == 3 && j == 0) ? wc : 1.f, a.M == 1, b - 1);
       __syncthreads();
-      block_fft<LOGB, NT, -1>(A);
+      block_fft<LOGB, NT, -1>(A, tw);
       for (int f = tid; f < b; f += NT) {
         const float2 X = A[pad_idx(f)];
         float2 term;
@@ -373,7 +381,7 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB)) rank1_kernel(Rank1Args
   __syncthreads();
   float s = 1.f;
   if (a.domain == 0) {
-    block_fft<LOGB, NT, +1>(A);
+    block_fft<LOGB, NT, +1>(A, tw);
     s = 1.f / (float)b;
   }
   float2* Sm = a.S + (size_t)m * b;
