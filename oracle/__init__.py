@@ -12,6 +12,7 @@ Modules (each function cites the passage it follows):
   sketch   -- count sketches and tensor sketches by definition (Eq. 1, Eq. 4, Eq. 7, App. B)
   contract -- exact and sketched T(I,u,u), T(u,u,u), T(I,v,w) (Sec. 3.2, App. B)
   rtpm     -- plain and sketched robust tensor power method (Sec. 2, Alg. 1)
+  cp       -- sketched CP loss and gradient, sketched ALS update (Alg. 2, Eq. 15)
 
 Parity pins: every function is checked in tests/test_oracle_pins.py against facts fixed by
 the paper or by mathematics (collision-free exactness, Prop. 1, Lemma 1 unbiasedness and
@@ -26,3 +27,6 @@ from .contract import (exact_iuu, exact_uuu, exact_ivw, contract_iuu, contract_u
                        contract_iuu_def, contract_uuu_def, contract_ivw_asym)
 from .rtpm import (median, median_rows, rtpm_sketched, rtpm_exact, power_step_sketched,  # noqa: F401
                    eigenvalue_sketched, deflate_sketches, NonFiniteError)
+from . import cp  # noqa: F401,E402
+from .cp import (cp_sketch_loss, cp_sketch_grad, cp_exact_loss, contract_ivw_mode,  # noqa: F401,E402
+                 als_sketched_columns, als_solve)

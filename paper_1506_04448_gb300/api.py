@@ -285,3 +285,122 @@ def decompose_symmetric(T, k: int, L: int, T_iters: int, B: int, log2b: int, see
     if host:
         return {key: val.to("cpu") for key, val in res.items()}
     return res
+
+
+# ------------------------------------------------------------------ asymmetric sketches, CP fitting
+def sketch_rfft(S: torch.Tensor) -> torch.Tensor:
+    """Half spectra [B][b/2+1] of the real parts of complex64 sketches S [B][b]."""
+    device = S.device
+    _need(S, "S", torch.complex64, device)
+    B, b = S.shape
+    log2b = b.bit_length() - 1
+    Xh = torch.empty((B, b // 2 + 1), dtype=torch.complex64, device=device)
+    rc = _lib.load().sketch_rfft(_ctx(device), _ptr(S), _ptr(Xh), B, log2b)
+    _lib.check("sketch_rfft", rc)
+    return Xh
+
+
+def _asym_common(Xh, h, g, dims):
+    device = Xh.device
+    _need(Xh, "Xh", torch.complex64, device)
+    B, nh = Xh.shape
+    b = 2 * (nh - 1)
+    log2b = b.bit_length() - 1
+    if 1 << log2b != b:
+        raise ValueError("Xh must hold half spectra of a power-of-two sketch length")
+    _need(h, "h", torch.int32, device)
+    _need(g, "g", torch.uint8, device)
+    if h.dim() != 3 or h.shape[0] != B or h.shape[1] != 3 or h.shape != g.shape:
+        raise ValueError("asymmetric hash tables must have shape [B][3][nmax]")
+    dims = [int(d) for d in dims]
+    if max(dims) != h.shape[2]:
+        raise ValueError("max(dims) must equal h.shape[2]")
+    return device, B, log2b, dims
+
+
+def contract_ivw(Xh: torch.Tensor, h: torch.Tensor, g: torch.Tensor, dims, mode: int,
+                 V: torch.Tensor, W: torch.Tensor, return_all: bool = False):
+    """Sketched T^(I,v,w) with the identity at `mode` and V, W on the other two modes in
+    increasing order (Prop. 1; the columns of T_(1)(C (.) B) in Alg. 2); median over sketches."""
+    device, B, log2b, dims = _asym_common(Xh, h, g, dims)
+    others = [j for j in range(3) if j != mode]
+    K = V.shape[0]
+    _need(V, "V", torch.float32, device, (K, dims[others[0]]))
+    _need(W, "W", torch.float32, device, (K, dims[others[1]]))
+    Vmed = torch.empty((K, dims[mode]), dtype=torch.float32, device=device)
+    Vall = torch.empty((K, B, dims[mode]), dtype=torch.float32, device=device) if return_all else None
+    rc = _lib.load().contract_ivw(_ctx(device), _ptr(Xh), _ptr(h), _ptr(g), B, log2b, _dims(dims),
+                                  int(mode), _ptr(V), _ptr(W), K, _ptr(Vmed), _ptr(Vall))
+    _lib.check("contract_ivw", rc)
+    return (Vmed, Vall) if return_all else Vmed
+
+
+def cp_sketch_loss(Xh: torch.Tensor, h: torch.Tensor, g: torch.Tensor, dims, lam: torch.Tensor,
+                   A: torch.Tensor, Bf: torch.Tensor, C: torch.Tensor, with_grad: bool = True):
+    """Sketched CP loss (1/B) sum_m ||s_T^(m) - sum_r lam_r s^(m)_{A[r](x)Bf[r](x)C[r]}||^2 and,
+    with_grad, its gradients (lam, A, Bf, C) from the hand-written adjoint kernel."""
+    device, B, log2b, dims = _asym_common(Xh, h, g, dims)
+    R = lam.shape[0]
+    _need(lam, "lam", torch.float32, device, (R,))
+    for name, t, d in (("A", A, dims[0]), ("Bf", Bf, dims[1]), ("C", C, dims[2])):
+        _need(t, name, torch.float32, device, (R, d))
+    loss = torch.empty((), dtype=torch.float32, device=device)
+    grads = [torch.empty_like(t) for t in (lam, A, Bf, C)] if with_grad else [None] * 4
+    rc = _lib.load().cp_sketch_loss(_ctx(device), _ptr(Xh), _ptr(h), _ptr(g), B, log2b, _dims(dims),
+                                    R, _ptr(lam), _ptr(A), _ptr(Bf), _ptr(C), _ptr(loss),
+                                    *[_ptr(t) for t in grads])
+    _lib.check("cp_sketch_loss", rc)
+    return (loss, *grads) if with_grad else loss
+
+
+class CPSketchLoss(torch.autograd.Function):
+    """Differentiable sketched CP loss: forward and the adjoint both run in libtsk (the gradient
+    of each factor is a sketched T(I,v,w) contraction of the residual sketch)."""
+
+    @staticmethod
+    def forward(ctx, lam, A, Bf, C, Xh, h, g, dims):
+        loss, g_lam, g_A, g_B, g_C = cp_sketch_loss(Xh, h, g, dims, lam.detach().contiguous(),
+                                                    A.detach().contiguous(), Bf.detach().contiguous(),
+                                                    C.detach().contiguous(), with_grad=True)
+        ctx.save_for_backward(g_lam, g_A, g_B, g_C)
+        return loss
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        g_lam, g_A, g_B, g_C = ctx.saved_tensors
+        return grad_out * g_lam, grad_out * g_A, grad_out * g_B, grad_out * g_C, None, None, None, None
+
+
+def cp_loss(lam, A, Bf, C, Xh, h, g, dims):
+    """Autograd entry point of the sketched CP loss."""
+    return CPSketchLoss.apply(lam, A, Bf, C, Xh, h, g, tuple(int(d) for d in dims))
+
+
+def cp_als_solve(M: torch.Tensor, P: torch.Tensor, Q: torch.Tensor):
+    """Eq. 15: out = G^-1 M, G = (P P^T) o (Q Q^T); returns (normalised rows, row norms)."""
+    device = M.device
+    K, n = M.shape
+    _need(M, "M", torch.float32, device)
+    _need(P, "P", torch.float32, device)
+    _need(Q, "Q", torch.float32, device)
+    if P.shape[0] != K or Q.shape[0] != K:
+        raise ValueError("P and Q must have K rows")
+    out = torch.empty_like(M)
+    lam = torch.empty((K,), dtype=torch.float32, device=device)
+    rc = _lib.load().cp_als_solve(_ctx(device), _ptr(M), _ptr(P), _ptr(Q), K, n, P.shape[1],
+                                  Q.shape[1], _ptr(out), _ptr(lam))
+    _lib.check("cp_als_solve", rc)
+    return out, lam
+
+
+def cp_als_step(Xh, h, g, dims, factors):
+    """One sweep of the sketched ALS of Alg. 2 with the Gram inverse of Eq. 15: for each mode,
+    the sketched T(I, x_r, y_r) columns (median over sketches) and the k x k solve.  Returns
+    (lam, [A, Bf, C]) with unit-norm rows."""
+    factors = list(factors)
+    lam = None
+    for mode in range(3):
+        p, q = [j for j in range(3) if j != mode]
+        M = contract_ivw(Xh, h, g, dims, mode, factors[p], factors[q])
+        factors[mode], lam = cp_als_solve(M, factors[p], factors[q])
+    return lam, factors

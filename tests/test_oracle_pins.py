@@ -350,3 +350,89 @@ def test_sketched_rtpm_collision_free_equals_exact():
         assert sk["lam_all"][r, sk["tau"][r]] >= sk["lam_all"][r].max() - 1e-12
     np.testing.assert_allclose(sk["lam"], ex["lam"], rtol=1e-9)
     np.testing.assert_allclose(sk["V"], ex["V"], atol=1e-9)
+
+
+# ------------------------------------------------------------------ sketched CP loss, ALS (Alg. 2)
+def _injective_asym(n1, n2, n3):
+    """h1(i) = i, h2(j) = n1 j, h3(k) = n1 n2 k: H is injective on [n1] x [n2] x [n3]."""
+    nmax = max(n1, n2, n3)
+    h = np.zeros((3, nmax), dtype=np.int64)
+    h[0, :n1] = np.arange(n1)
+    h[1, :n2] = n1 * np.arange(n2)
+    h[2, :n3] = n1 * n2 * np.arange(n3)
+    b = 1 << int(np.ceil(np.log2(n1 * n2 * n3)))
+    return h, b
+
+
+def _cp_problem(seed, dims, R):
+    r = synth.rng(seed)
+    T = r.standard_normal(dims)
+    lam = r.uniform(0.5, 2.0, R)
+    A, Bf, C = (r.standard_normal((R, d)) for d in dims)
+    return T, lam, A, Bf, C
+
+
+def test_cp_sketched_loss_is_exact_without_collisions():
+    dims = (4, 3, 5)
+    h1, b = _injective_asym(*dims)
+    T, lam, A, Bf, C = _cp_problem(1, dims, 3)
+    g = synth.rng(2).integers(0, 4, size=(2, 3, h1.shape[1]))
+    h = np.stack([h1, h1])
+    S = np.stack([O.sketch_tensor_asym(T, h[m], g[m], b) for m in range(2)])
+    assert abs(O.cp_sketch_loss(S, h, g, b, lam, A, Bf, C) - O.cp_exact_loss(T, lam, A, Bf, C)) < 1e-9
+
+
+@pytest.mark.parametrize("step", [1e-3, 1e-5])
+def test_cp_gradient_matches_central_differences(step):
+    dims = (5, 4, 3)
+    b = 32
+    h, g = O.cs_hashes(3, 2, 5, list(dims))
+    T, lam, A, Bf, C = _cp_problem(4, dims, 2)
+    S = np.stack([O.sketch_tensor_asym(T, h[m], g[m], b) for m in range(2)])
+    grads = O.cp_sketch_grad(S, h, g, b, lam, A, Bf, C)
+    params = [lam, A, Bf, C]
+
+    def loss(ps):
+        return O.cp_sketch_loss(S, h, g, b, *ps)
+    for which in range(4):
+        fd = np.zeros_like(params[which])
+        for idx in np.ndindex(params[which].shape):
+            up = [p.copy() for p in params]
+            dn = [p.copy() for p in params]
+            up[which][idx] += step
+            dn[which][idx] -= step
+            fd[idx] = (loss(up) - loss(dn)) / (2 * step)
+        np.testing.assert_allclose(fd, grads[which], rtol=1e-4, atol=1e-4 * np.max(np.abs(grads[which])))
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_asymmetric_ivw_is_exact_without_collisions(mode):
+    dims = (4, 3, 5)
+    h, b = _injective_asym(*dims)
+    g = synth.rng(5).integers(0, 4, size=(3, h.shape[1]))
+    T = synth.rng(6).standard_normal(dims)
+    others = [j for j in range(3) if j != mode]
+    V = synth.random_vector(dims[others[0]], 7)
+    W = synth.random_vector(dims[others[1]], 8)
+    S = O.sketch_tensor_asym(T, h, g, b)
+    want = np.einsum("ijk->" + "ijk"[mode] + "".join("ijk"[o] for o in others), T)
+    want = np.einsum("xab,a,b->x", want, V, W)
+    np.testing.assert_allclose(O.contract_ivw_mode(S, h, g, b, mode, V, W, dims[mode]), want,
+                               rtol=1e-12, atol=1e-12)
+
+
+def test_sketched_als_update_equals_exact_update_without_collisions():
+    """With exact T(I, b_r, c_r) columns, Alg. 2 with Eq. 15 is the plain ALS step."""
+    dims = (4, 3, 5)
+    h1, b = _injective_asym(*dims)
+    T, lam, A, Bf, C = _cp_problem(9, dims, 2)
+    h = np.stack([h1] * 3)
+    g = synth.rng(10).integers(0, 4, size=(3, 3, h1.shape[1]))
+    S = np.stack([O.sketch_tensor_asym(T, h[m], g[m], b) for m in range(3)])
+    M = O.als_sketched_columns(S, h, g, b, 0, (A, Bf, C))
+    T1 = T.reshape(dims[0], -1)                                    # mode-1 unfolding, j-major
+    KR = np.stack([np.kron(Bf[r], C[r]) for r in range(2)], axis=1)  # columns b_r (x) c_r
+    np.testing.assert_allclose(M.T, T1 @ KR, rtol=1e-10, atol=1e-10)
+    out, lam_new = O.als_solve(M, Bf, C)
+    ref = (T1 @ KR) @ np.linalg.pinv((Bf @ Bf.T) * (C @ C.T))      # Eq. 15
+    np.testing.assert_allclose(out.T * lam_new, ref, rtol=1e-9, atol=1e-9)
