@@ -225,6 +225,47 @@ int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* h, const ui
                         double* lambda, float* Vout, int32_t* tau_star, float* S_deflated,
                         float* lam_all, float* U_iters);
 
+/* ---------------------------------------------------------------- many independent problems */
+
+/* One decomposition of a batch (all pointers device memory; see robust_power_method). */
+typedef struct tsk_problem {
+  const float* S;      /* [B][b] TSK_C64 time-domain colliding sketches (read only) */
+  const int32_t* h;    /* [B][n] */
+  const uint8_t* g;    /* [B][n] */
+  const float* U0;     /* [k][L][n] initial vectors (NULL allowed when k = 0) */
+  int64_t n;           /* dimension, 1..8192 */
+  int k;               /* deflation rounds, >= 0 */
+  int log2b;           /* sketch length 2^log2b, 10..14 */
+  double* lambda;      /* out [k] */
+  float* V;            /* out [k][n] */
+  int32_t* tau;        /* out [k] or NULL */
+  float* lam_all;      /* out [k][L] or NULL: lambda_tau of every round */
+  float* U_iters;      /* out [k][T][L][n] or NULL: every iterate */
+} tsk_problem;
+
+typedef struct tsk_batch tsk_batch;
+
+/* Plan Alg. 1 for P independent problems sharing B, L and T (the batch pattern of many
+ * decompositions of uneven size; the paper runs one decomposition at a time).  Problems are
+ * grouped by sketch length; each group's power steps are single launches over all its active
+ * problems, groups run on helper streams of the context.  The plan allocates its own workspace
+ * (device memory, freed by tsk_batch_destroy) and copies the problem descriptors to the device;
+ * autotune = 1 times each compiled block size (FFT elements per thread) of every group on its
+ * first power step and keeps the fastest.  The problem arrays must stay valid until the plan
+ * is destroyed. */
+int tsk_batch_create(tsk_ctx* ctx, const tsk_problem* problems, int P, int B, int L, int T,
+                     int autotune, tsk_batch** out);
+/* Enqueue the whole batch on the context's stream (sketch copies, DFTs, all rounds of every
+ * problem).  Allocates nothing and synchronises nothing, so it can be captured into one CUDA
+ * graph and replayed; each run starts from the problems' S and U0 again. */
+int tsk_batch_run(tsk_ctx* ctx, tsk_batch* batch);
+int tsk_batch_destroy(tsk_batch* batch);
+/* Block size chosen for the group of sketch length 2^log2b (0 if the plan has no such group). */
+int tsk_batch_block_size(const tsk_batch* batch, int log2b);
+/* create (without autotuning) + run + synchronise + destroy. */
+int robust_power_method_batched(tsk_ctx* ctx, const tsk_problem* problems, int P, int B, int L,
+                                int T);
+
 #ifdef __cplusplus
 }
 #endif

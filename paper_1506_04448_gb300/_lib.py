@@ -37,6 +37,11 @@ SIGNATURES = {
     "contract_ivw": (_I, [_P, _P, _P, _P, _I, _I, _P, _I, _P, _P, _I, _P, _P]),
     "cp_sketch_loss": (_I, [_P, _P, _P, _P, _I, _I, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "cp_als_solve": (_I, [_P, _P, _P, _P, _I, _I64, _I64, _I64, _P, _P]),
+    "tsk_batch_create": (_I, [_P, _P, _I, _I, _I, _I, _I, ctypes.POINTER(_P)]),
+    "tsk_batch_run": (_I, [_P, _P]),
+    "tsk_batch_destroy": (_I, [_P]),
+    "tsk_batch_block_size": (_I, [_P, _I]),
+    "robust_power_method_batched": (_I, [_P, _P, _I, _I, _I, _I]),
     "robust_power_method": (_I, [_P, _P, _P, _P, _I, _I, _I64, _I, _I, _I, _P, _P, _P, _P, _P,
                                  _P, _P]),
 }

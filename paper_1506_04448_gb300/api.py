@@ -404,3 +404,77 @@ def cp_als_step(Xh, h, g, dims, factors):
         M = contract_ivw(Xh, h, g, dims, mode, factors[p], factors[q])
         factors[mode], lam = cp_als_solve(M, factors[p], factors[q])
     return lam, factors
+
+
+# ------------------------------------------------------------------ many independent problems
+class _Problem(ctypes.Structure):
+    """Mirror of tsk_problem in include/tsk.h."""
+    _fields_ = [("S", ctypes.c_void_p), ("h", ctypes.c_void_p), ("g", ctypes.c_void_p),
+                ("U0", ctypes.c_void_p), ("n", ctypes.c_int64), ("k", ctypes.c_int),
+                ("log2b", ctypes.c_int), ("lam", ctypes.c_void_p), ("V", ctypes.c_void_p),
+                ("tau", ctypes.c_void_p), ("lam_all", ctypes.c_void_p), ("U_iters", ctypes.c_void_p)]
+
+
+class BatchPlan:
+    """Alg. 1 for many independent problems (uneven n, k, b) sharing B, L and T.
+
+    problems: list of dicts with keys S ([B][b] complex64 colliding sketches), h, g ([B][n] or
+    [B][1][n]) and U0 ([k][L][n] float32), all on one CUDA device.  run() only enqueues work on
+    the current stream (capturable into a CUDA graph); results[i] holds lam, V, tau (and, with
+    trace=True, lam_all and U_iters) of problem i after the stream has synchronised."""
+
+    def __init__(self, problems, B: int, L: int, T: int, autotune: bool = True, trace: bool = False):
+        self.lib = _lib.load()
+        self.device = problems[0]["S"].device
+        self.B, self.L, self.T = B, L, T
+        self._keep = []
+        self.results = []
+        arr = (_Problem * len(problems))()
+        for i, p in enumerate(problems):
+            S = _need(p["S"], "S", torch.complex64, self.device)
+            h, g = _hashes_shape(p["h"], p["g"])
+            _need(h, "h", torch.int32, self.device)
+            _need(g, "g", torch.uint8, self.device)
+            U0 = _need(p["U0"], "U0", torch.float32, self.device)
+            k, L_, n = U0.shape
+            if S.shape[0] != B or L_ != L or h.shape != (B, 1, n):
+                raise ValueError(f"problem {i}: shapes do not match B={B}, L={L}")
+            b = S.shape[1]
+            res = {"lam": torch.empty((k,), dtype=torch.float64, device=self.device),
+                   "V": torch.empty((k, n), dtype=torch.float32, device=self.device),
+                   "tau": torch.empty((k,), dtype=torch.int32, device=self.device)}
+            if trace:
+                res["lam_all"] = torch.empty((k, L), dtype=torch.float32, device=self.device)
+                res["U_iters"] = torch.empty((k, T, L, n), dtype=torch.float32, device=self.device)
+            self.results.append(res)
+            self._keep.extend([S, h, g, U0])
+            arr[i] = _Problem(S.data_ptr(), h.data_ptr(), g.data_ptr(), U0.data_ptr(), n, k,
+                              b.bit_length() - 1, res["lam"].data_ptr(), res["V"].data_ptr(),
+                              res["tau"].data_ptr(),
+                              res["lam_all"].data_ptr() if trace else 0,
+                              res["U_iters"].data_ptr() if trace else 0)
+        self._arr = arr
+        handle = ctypes.c_void_p()
+        rc = self.lib.tsk_batch_create(_ctx(self.device), arr, len(problems), B, L, T,
+                                       int(bool(autotune)), ctypes.byref(handle))
+        _lib.check("tsk_batch_create", rc)
+        self.handle = handle.value
+
+    def block_size(self, log2b: int) -> int:
+        return self.lib.tsk_batch_block_size(ctypes.c_void_p(self.handle), log2b)
+
+    def run(self) -> None:
+        rc = self.lib.tsk_batch_run(_ctx(self.device), ctypes.c_void_p(self.handle))
+        _lib.check("tsk_batch_run", rc)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            torch.cuda.synchronize(self.device)
+            self.lib.tsk_batch_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -328,17 +328,11 @@ __global__ void __launch_bounds__(256) als_solve_kernel(const float* M, const fl
 }
 
 // ------------------------------------------------------------------ launch helpers
-template <typename Kern>
-static int set_smem(Kern k, size_t smem) {
-  TSK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  return TSK_OK;
-}
 
 template <int LOGB>
 static int launch_rfft_t(const float2* S, float2* Xh, int B, cudaStream_t st) {
   constexpr size_t smem = asym_smem_bytes<LOGB>();
-  int rc = set_smem(rfft_rows_kernel<LOGB>, smem);
-  if (rc != TSK_OK) return rc;
+  TSK_CUDA(tsk_smem_attr<rfft_rows_kernel<LOGB>>(smem));
   rfft_rows_kernel<LOGB><<<B, asym_threads<LOGB>(), smem, st>>>(S, Xh);
   TSK_CHECK_LAUNCH();
   return TSK_OK;
@@ -347,8 +341,7 @@ static int launch_rfft_t(const float2* S, float2* Xh, int B, cudaStream_t st) {
 template <int LOGB>
 static int launch_ivw_t(const IvwArgs& a, cudaStream_t st) {
   constexpr size_t smem = asym_smem_bytes<LOGB>();
-  int rc = set_smem(ivw_kernel<LOGB>, smem);
-  if (rc != TSK_OK) return rc;
+  TSK_CUDA(tsk_smem_attr<ivw_kernel<LOGB>>(smem));
   ivw_kernel<LOGB><<<dim3(a.B, a.K), asym_threads<LOGB>(), smem, st>>>(a);
   TSK_CHECK_LAUNCH();
   return TSK_OK;
@@ -358,16 +351,14 @@ template <int LOGB>
 static int launch_cp_t(const CpArgs& a, bool with_grad, cudaStream_t st) {
   constexpr size_t smem = asym_smem_bytes<LOGB>();
   constexpr int N = 1 << (LOGB - 1);
-  int rc = set_smem(cp_spectra_kernel<LOGB>, smem);
-  if (rc != TSK_OK) return rc;
+  TSK_CUDA(tsk_smem_attr<cp_spectra_kernel<LOGB>>(smem));
   cp_spectra_kernel<LOGB><<<dim3(a.B, a.R, 3), asym_threads<LOGB>(), smem, st>>>(a);
   TSK_CHECK_LAUNCH();
   const int chunks = (N + 1 + 255) / 256 < 64 ? (N + 1 + 255) / 256 : 64;
   cp_residual_kernel<<<dim3(a.B, chunks), 256, 0, st>>>(a, N);
   TSK_CHECK_LAUNCH();
   if (with_grad) {
-    rc = set_smem(cp_adjoint_kernel<LOGB>, smem);
-    if (rc != TSK_OK) return rc;
+    TSK_CUDA(tsk_smem_attr<cp_adjoint_kernel<LOGB>>(smem));
     cp_adjoint_kernel<LOGB><<<dim3(a.B, a.R, 3), asym_threads<LOGB>(), smem, st>>>(a);
     TSK_CHECK_LAUNCH();
   }

@@ -70,6 +70,22 @@ int tsk_ws_reserve(tsk_ctx* ctx, size_t bytes);
 // Make sure `count` helper streams and their events exist.
 int tsk_ctx_aux_streams(tsk_ctx* ctx, int count);
 
+// Raise KERNEL's dynamic shared-memory limit to `smem` once per device.  The attribute call is
+// not a stream operation; doing it once (on the first, uncaptured launch) keeps later launch
+// sequences capturable into CUDA graphs.  For kernels whose shared memory does not vary.
+template <auto KERNEL>
+inline cudaError_t tsk_smem_attr(size_t smem) {
+  static unsigned long long done = 0;   // bit d set once device d is configured
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (__atomic_load_n(&done, __ATOMIC_ACQUIRE) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) __atomic_fetch_or(&done, bit, __ATOMIC_RELEASE);
+  return e;
+}
+
 // Map a CUDA error to a tsk status.
 inline int tsk_from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return TSK_OK;
@@ -83,9 +99,9 @@ inline int tsk_from_cuda(cudaError_t e) {
     if (e_ != cudaSuccess) return tsk_from_cuda(e_);          \
   } while (0)
 
-#define TSK_CUDA(call)                                        \
+#define TSK_CUDA(...)                                         \
   do {                                                        \
-    cudaError_t e_ = (call);                                  \
+    cudaError_t e_ = (__VA_ARGS__);                           \
     if (e_ != cudaSuccess) return tsk_from_cuda(e_);          \
   } while (0)
 

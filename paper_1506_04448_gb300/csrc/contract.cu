@@ -10,8 +10,7 @@ template <int LOGB, int MODE>
 static int launch_contract_t(const ContractArgs& a, cudaStream_t st) {
   constexpr int NT = threads_for_logb(LOGB);
   constexpr size_t smem = contract_smem_bytes<LOGB>();
-  TSK_CUDA(cudaFuncSetAttribute(contract_kernel<LOGB, MODE>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TSK_CUDA(tsk_smem_attr<contract_kernel<LOGB, MODE>>(smem));
   dim3 grid(a.B, a.L);
   contract_kernel<LOGB, MODE><<<grid, NT, smem, st>>>(a);
   TSK_CHECK_LAUNCH();
@@ -41,8 +40,7 @@ template <int LOGB>
 static int launch_deflate_t(const DeflateArgs& a, int B, cudaStream_t st) {
   constexpr int NT = threads_for_logb(LOGB);
   constexpr size_t smem = (size_t)padded_len(1 << LOGB) * sizeof(float2);
-  TSK_CUDA(cudaFuncSetAttribute(deflate_kernel<LOGB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
+  TSK_CUDA(tsk_smem_attr<deflate_kernel<LOGB>>(smem));
   deflate_kernel<LOGB><<<B, NT, smem, st>>>(a);
   TSK_CHECK_LAUNCH();
   return TSK_OK;

@@ -58,13 +58,12 @@ constexpr size_t contract_smem_bytes() {
 
 // One (vector, sketch) contraction.  MODE_IUU writes v^(m) to vout[0..n); both modes return
 // lambda^(m) = T^(m)(u,u,u) in every thread.  Must be called by all NT threads of the block.
-template <int LOGB, int MODE>
+template <int LOGB, int MODE, int NT = threads_for_logb(LOGB)>
 __device__ __forceinline__ float contract_one(float2* A, float2* Eb, float* red, const float2* tw,
                                               const float2* FSm, const float2* Sm,
                                               const int32_t* hm, const uint8_t* gm,
                                               const float* u, int n, bool normalize, int* status,
                                               float* vout) {
-  constexpr int NT = threads_for_logb(LOGB);
   constexpr int b = 1 << LOGB;
   constexpr int hb = b / 2;
   constexpr float inv_b = 1.f / (float)b;
@@ -201,11 +200,10 @@ __device__ __forceinline__ float median_of(const float* x, int B) {
 
 // Deflation of one sketch by lambda^ u(x)u(x)u (Alg. 1, deflation step; Sec. 3.3):
 //   U = F s~_u,  D = lambda^ U^3,  FS[m] -= D,  S[m] -= F^-1 D.
-template <int LOGB>
+template <int LOGB, int NT = threads_for_logb(LOGB)>
 __device__ __forceinline__ void deflate_one(float2* A, const float2* tw, float2* FSm, float2* Sm,
                                             const int32_t* hm,
                                             const uint8_t* gm, const float* u, int n, float lam) {
-  constexpr int NT = threads_for_logb(LOGB);
   constexpr int b = 1 << LOGB;
   const int tid = threadIdx.x;
   for (int i = tid; i < padded_len(b); i += NT) A[i] = make_float2(0.f, 0.f);

@@ -279,8 +279,7 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB)) fft_rows_kernel(const 
 template <int LOGB>
 static int launch_fft_t(const float2* in, float2* out, int B, int inverse, cudaStream_t st) {
   constexpr size_t smem = (size_t)padded_len(1 << LOGB) * sizeof(float2);
-  TSK_CUDA(cudaFuncSetAttribute(fft_rows_kernel<LOGB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
+  TSK_CUDA(tsk_smem_attr<fft_rows_kernel<LOGB>>(smem));
   fft_rows_kernel<LOGB><<<B, threads_for_logb(LOGB), smem, st>>>(in, out, inverse);
   TSK_CHECK_LAUNCH();
   return TSK_OK;
@@ -394,8 +393,7 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB)) rank1_kernel(Rank1Args
 template <int LOGB>
 static int launch_rank1_t(const Rank1Args& a, int B, cudaStream_t st) {
   constexpr size_t smem = (size_t)padded_len(1 << LOGB) * sizeof(float2);
-  TSK_CUDA(cudaFuncSetAttribute(rank1_kernel<LOGB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
+  TSK_CUDA(tsk_smem_attr<rank1_kernel<LOGB>>(smem));
   rank1_kernel<LOGB><<<B, threads_for_logb(LOGB), smem, st>>>(a);
   TSK_CHECK_LAUNCH();
   return TSK_OK;

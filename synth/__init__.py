@@ -95,3 +95,19 @@ def gaussian_inits(k: int, L: int, n: int, seed: int) -> np.ndarray:
 
 def random_vector(n: int, seed: int) -> np.ndarray:
     return rng(seed).standard_normal(n)
+
+
+def batched_problem_specs(P: int, seed: int, n_low: int = 32, n_high: int = 256, k_low: int = 4,
+                          k_high: int = 16, log2b_low: int = 10, log2b_high: int = 14):
+    """Sizes of P independent planted problems: n ~ U{n_low..n_high}, k ~ U{k_low..k_high},
+    sketch length b = 2^ceil(log2(n k)) clamped to [2^log2b_low, 2^log2b_high].  Returns a list of
+    dicts (n, k, log2b, seed) with a per-problem seed for planted_symmetric / gaussian_inits."""
+    r = rng(seed)
+    specs = []
+    for p in range(P):
+        n = int(r.integers(n_low, n_high + 1))
+        k = int(r.integers(k_low, k_high + 1))
+        log2b = int(np.ceil(np.log2(n * k)))
+        log2b = min(max(log2b, log2b_low), log2b_high)
+        specs.append({"n": n, "k": k, "log2b": log2b, "seed": int(seed * 100003 + p)})
+    return specs
