@@ -13,6 +13,7 @@ Modules (each function cites the passage it follows):
   contract -- exact and sketched T(I,u,u), T(u,u,u), T(I,v,w) (Sec. 3.2, App. B)
   rtpm     -- plain and sketched robust tensor power method (Sec. 2, Alg. 1)
   cp       -- sketched CP loss and gradient, sketched ALS update (Alg. 2, Eq. 15)
+  lda      -- spectral LDA moments, whitening, whitened M3, recovery (App. D, Alg. 3)
 
 Parity pins: every function is checked in tests/test_oracle_pins.py against facts fixed by
 the paper or by mathematics (collision-free exactness, Prop. 1, Lemma 1 unbiasedness and
@@ -30,3 +31,4 @@ from .rtpm import (median, median_rows, rtpm_sketched, rtpm_exact, power_step_sk
 from . import cp  # noqa: F401,E402
 from .cp import (cp_sketch_loss, cp_sketch_grad, cp_exact_loss, contract_ivw_mode,  # noqa: F401,E402
                  als_sketched_columns, als_solve)
+from . import lda  # noqa: F401,E402

@@ -111,3 +111,40 @@ def batched_problem_specs(P: int, seed: int, n_low: int = 32, n_high: int = 256,
         log2b = min(max(log2b, log2b_low), log2b_high)
         specs.append({"n": n, "k": k, "log2b": log2b, "seed": int(seed * 100003 + p)})
     return specs
+
+
+def lda_corpus(V: int, k: int, D: int, seed: int, alpha: float = 0.1, beta: float = 0.01,
+               mean_len: float = 200.0):
+    """Synthetic LDA corpus (the generative model of App. D): topic-word distributions
+    Phi[t] ~ Dir(beta 1_V), document mixtures theta_d ~ Dir(alpha 1_k), lengths m_d ~ Poisson,
+    topic counts per document ~ Multinomial(m_d, theta_d), words of topic t ~ Cat(Phi[t]).
+    Returns dict(indptr int64 [D+1], idx int32 [nnz], cnt int32 [nnz], Phi [k][V], alpha [k],
+    lengths [D]) with each document's words sorted and counted (CSR)."""
+    r = rng(seed)
+    Phi = r.dirichlet(np.full(V, beta), size=k)
+    alpha_vec = np.full(k, alpha)
+    theta = r.dirichlet(alpha_vec, size=D)
+    lengths = r.poisson(mean_len, size=D).astype(np.int64)
+    topic_counts = r.multinomial(lengths, theta)                     # D x k
+    doc_of, word_of = [], []
+    for t in range(k):
+        ct = topic_counts[:, t]
+        tot = int(ct.sum())
+        if tot == 0:
+            continue
+        doc_of.append(np.repeat(np.arange(D, dtype=np.int64), ct))
+        word_of.append(r.choice(V, size=tot, p=Phi[t]).astype(np.int64))
+    doc_of = np.concatenate(doc_of)
+    word_of = np.concatenate(word_of)
+    keys, cnt = np.unique(doc_of * V + word_of, return_counts=True)
+    docs = keys // V
+    indptr = np.zeros(D + 1, dtype=np.int64)
+    np.add.at(indptr, docs + 1, 1)
+    indptr = np.cumsum(indptr)
+    return {"indptr": indptr, "idx": (keys % V).astype(np.int32), "cnt": cnt.astype(np.int32),
+            "Phi": Phi, "alpha": alpha_vec, "lengths": lengths, "V": V, "k": k, "D": D}
+
+
+def gaussian_matrix(rows: int, cols: int, seed: int) -> np.ndarray:
+    """Standard Gaussian test matrix (the random start of a randomized range finder)."""
+    return rng(seed).standard_normal((rows, cols))
