@@ -205,6 +205,62 @@ int cp_sketch_loss(tsk_ctx* ctx, const float* Xh, const int32_t* h, const uint8_
 int cp_als_solve(tsk_ctx* ctx, const float* M, const float* P, const float* Q, int K, int64_t n,
                  int64_t np, int64_t nq, float* out, float* lam);
 
+/* ---------------------------------------------------------------- spectral LDA (App. D, Alg. 3) */
+
+/* Corpora are CSR word counts on the device: indptr int64 [D+1] (indptr[0] = 0, nondecreasing),
+ * idx int32 [nnz] word ids in [0, V), cnt int32 [nnz] counts >= 1, nnz = indptr[D]; document d
+ * has length m_d = sum of its counts.  The empirical moments average per-document unbiased
+ * estimates over DISTINCT token positions (App. D):
+ *   M1^ = mean over documents with m_d >= 1 of n_d / m_d                        (Eq. moment1)
+ *   E2^ = mean over m_d >= 2 of (n_d n_d^T - diag n_d) / (m_d (m_d - 1))
+ *   E3^ = mean over m_d >= 3 of N_d, the ordered distinct-position triple counts
+ *         (n_i n_j n_k off the diagonals, n_i (n_i - 1) n_k on one, n_i (n_i-1)(n_i-2) on all)
+ *         / (m_d (m_d - 1)(m_d - 2))
+ *   M2^ = E2^ - alpha0/(alpha0+1) M1^ M1^T                                       (Eq. moment2)
+ *   M3^ = E3^ - alpha0/(alpha0+2) (E2^ (x) M1^ + the two other placements)
+ *         + 2 alpha0^2/((alpha0+1)(alpha0+2)) M1^ (x) M1^ (x) M1^                (Eq. moment3)
+ * Word ids outside [0, V) and counts < 1 are skipped and reported by tsk_ctx_status() as
+ * TSK_EINVAL. */
+
+/* Y = M2^ X without forming M2^.  X, Y: [V][c] float row-major.  Limits: 1 <= c <= 256. */
+int lda_m2_apply(tsk_ctx* ctx, const int64_t* indptr, const int32_t* idx, const int32_t* cnt,
+                 int64_t D, int64_t V, double alpha0, const float* X, int c, float* Y);
+
+/* Whitening (Alg. 3, line 3): the k leading eigenpairs (U, sigma) of M2^ by randomized
+ * subspace iteration from the start block Omega ([V][c] float, c = k + oversampling; random
+ * numbers are the caller's), power_iters extra applications of M2^, Cholesky-QR
+ * orthonormalisation, and a Rayleigh-Ritz step solved by FP64 Jacobi; then
+ * W[i][j] = U[i][j] / sqrt(sigma_j), so that W^T M2^ W = I_k.
+ * Outputs: W [V][k] float, sigma [k] double (descending), M1_out optional [V] float (M1^).
+ * Fewer than k positive Ritz values is reported by tsk_ctx_status() as TSK_EINVAL, a
+ * Cholesky breakdown as TSK_ENONFINITE.  Limits: 1 <= k <= c <= min(V, 128), power_iters <= 64. */
+int lda_whiten(tsk_ctx* ctx, const int64_t* indptr, const int32_t* idx, const int32_t* cnt,
+               int64_t D, int64_t V, int k, double alpha0, const float* Omega, int c,
+               int power_iters, float* W, double* sigma, float* M1_out);
+
+/* The whitened third moment M3^(W, W, W) (k x k x k, dense, symmetric, float) of Alg. 3,
+ * line 4, with each document entering through p_d = W^T n_d (Eq. td):
+ *   N_d(W,W,W) = p^(x)3 - sum_i n_i (w_i w_i p + w_i p w_i + p w_i w_i) + 2 sum_i n_i w_i^(x)3,
+ * w_i = row i of W, and E2^(W, W) (x) q with q = W^T M1^ for the alpha0 terms (Eq. applda_exxm).
+ * W: [V][k] float.  Accumulates in FP32 over at most ~4096 documents, then in FP64.
+ * Limits: 1 <= k <= 256. */
+int lda_whitened_m3(tsk_ctx* ctx, const int64_t* indptr, const int32_t* idx, const int32_t* cnt,
+                    int64_t D, int64_t V, const float* W, int k, double alpha0, float* M3);
+
+/* B colliding sketches of M3^(W, W, W) (Alg. 3, line 4): lda_whitened_m3 into M3 (caller's
+ * [k][k][k] float, also an output), then sketch_tensor with M = 1 into S ([B][b] TSK_C64).
+ * h, g: [B][k] hash tables (cs_hashes with M = 1, dims = {k}).  Limits: k <= 256, log2b <= 14. */
+int lda_sketch_m3(tsk_ctx* ctx, const int64_t* indptr, const int32_t* idx, const int32_t* cnt,
+                  int64_t D, int64_t V, const float* W, int k, double alpha0, const int32_t* h,
+                  const uint8_t* g, int B, int log2b, float* M3, float* S);
+
+/* Recovery (Alg. 3, line 6): alpha_hat[i] = 4 alpha0 (alpha0+1) / ((alpha0+2)^2 lambda_i^2) and
+ * mu_hat[i] = (alpha0+2)/2 lambda_i (W^+)^T v_i, with W^+ = (W^T W)^-1 W^T (FP64 Cholesky).
+ * W: [V][k] float; lambda: [k] double; Vv: [k][k] float, row i = v_i (robust_power_method's
+ * Vout); alpha_hat: [k] double; mu_hat: [k][V] float, row i = topic i.  Limits: k <= 128. */
+int lda_recover(tsk_ctx* ctx, const float* W, int64_t V, int k, double alpha0,
+                const double* lambda, const float* Vv, double* alpha_hat, float* mu_hat);
+
 /* ---------------------------------------------------------------- Alg. 1 */
 
 /* Fast robust tensor power method (Alg. 1) on B colliding sketches of a symmetric tensor.

@@ -20,6 +20,7 @@ _P = ctypes.c_void_p
 _I = ctypes.c_int
 _I64 = ctypes.c_int64
 _U64 = ctypes.c_uint64
+_D = ctypes.c_double
 SIGNATURES = {
     "tsk_ctx_create": (_I, [_I, _P, ctypes.POINTER(_P)]),
     "tsk_ctx_destroy": (_I, [_P]),
@@ -44,6 +45,11 @@ SIGNATURES = {
     "robust_power_method_batched": (_I, [_P, _P, _I, _I, _I, _I]),
     "robust_power_method": (_I, [_P, _P, _P, _P, _I, _I, _I64, _I, _I, _I, _P, _P, _P, _P, _P,
                                  _P, _P]),
+    "lda_m2_apply": (_I, [_P, _P, _P, _P, _I64, _I64, _D, _P, _I, _P]),
+    "lda_whiten": (_I, [_P, _P, _P, _P, _I64, _I64, _I, _D, _P, _I, _I, _P, _P, _P]),
+    "lda_whitened_m3": (_I, [_P, _P, _P, _P, _I64, _I64, _P, _I, _D, _P]),
+    "lda_sketch_m3": (_I, [_P, _P, _P, _P, _I64, _I64, _P, _I, _D, _P, _P, _I, _I, _P, _P]),
+    "lda_recover": (_I, [_P, _P, _I64, _I, _D, _P, _P, _P, _P]),
 }
 
 

@@ -478,3 +478,120 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ spectral LDA (App. D, Alg. 3)
+def _corpus(indptr: torch.Tensor, idx: torch.Tensor, cnt: torch.Tensor, V: int):
+    """Check a device CSR corpus; returns (device, D, idx, cnt) with a one-element stand-in for
+    empty idx/cnt arrays (the library wants non-null pointers)."""
+    device = indptr.device
+    _need(indptr, "indptr", torch.int64, device)
+    if indptr.dim() != 1 or indptr.numel() < 1:
+        raise ValueError("indptr must be a 1-D int64 tensor of D + 1 offsets")
+    _need(idx, "idx", torch.int32, device)
+    _need(cnt, "cnt", torch.int32, device)
+    if idx.shape != cnt.shape or idx.dim() != 1:
+        raise ValueError("idx and cnt must be 1-D of equal length")
+    if idx.numel() == 0:
+        idx = torch.zeros(1, dtype=torch.int32, device=device)
+        cnt = torch.ones(1, dtype=torch.int32, device=device)
+    if int(V) < 1:
+        raise ValueError("V must be >= 1")
+    return device, indptr.numel() - 1, idx, cnt
+
+
+def lda_m2_apply(indptr, idx, cnt, V: int, alpha0: float, X: torch.Tensor) -> torch.Tensor:
+    """M2^ X (Eq. moment2) for X [V][c] without forming M2^."""
+    device, D, idx, cnt = _corpus(indptr, idx, cnt, V)
+    _need(X, "X", torch.float32, device)
+    c = X.shape[1]
+    if X.shape[0] != V:
+        raise ValueError("X must have V rows")
+    Y = torch.empty_like(X)
+    rc = _lib.load().lda_m2_apply(_ctx(device), _ptr(indptr), _ptr(idx), _ptr(cnt), D, V,
+                                  float(alpha0), _ptr(X), c, _ptr(Y))
+    _lib.check("lda_m2_apply", rc)
+    return Y
+
+
+def lda_whiten(indptr, idx, cnt, V: int, k: int, alpha0: float, Omega: torch.Tensor,
+               power_iters: int = 2):
+    """Alg. 3, line 3: W [V][k] with W^T M2^ W = I from the k leading eigenpairs of M2^
+    (randomized subspace iteration from Omega [V][c]).  Returns (W, sigma [k] float64, M1 [V])."""
+    device, D, idx, cnt = _corpus(indptr, idx, cnt, V)
+    _need(Omega, "Omega", torch.float32, device)
+    if Omega.dim() != 2 or Omega.shape[0] != V:
+        raise ValueError("Omega must be [V][c]")
+    c = Omega.shape[1]
+    W = torch.empty((V, k), dtype=torch.float32, device=device)
+    sigma = torch.empty((k,), dtype=torch.float64, device=device)
+    M1 = torch.empty((V,), dtype=torch.float32, device=device)
+    rc = _lib.load().lda_whiten(_ctx(device), _ptr(indptr), _ptr(idx), _ptr(cnt), D, V, k,
+                                float(alpha0), _ptr(Omega), c, int(power_iters), _ptr(W),
+                                _ptr(sigma), _ptr(M1))
+    _lib.check("lda_whiten", rc)
+    return W, sigma, M1
+
+
+def lda_whitened_m3(indptr, idx, cnt, V: int, W: torch.Tensor, alpha0: float) -> torch.Tensor:
+    """M3^(W, W, W), dense k x k x k (Alg. 3, line 4; Eq. moment3 with Eq. td)."""
+    device, D, idx, cnt = _corpus(indptr, idx, cnt, V)
+    _need(W, "W", torch.float32, device)
+    if W.dim() != 2 or W.shape[0] != V:
+        raise ValueError("W must be [V][k]")
+    k = W.shape[1]
+    M3 = torch.empty((k, k, k), dtype=torch.float32, device=device)
+    rc = _lib.load().lda_whitened_m3(_ctx(device), _ptr(indptr), _ptr(idx), _ptr(cnt), D, V,
+                                     _ptr(W), k, float(alpha0), _ptr(M3))
+    _lib.check("lda_whitened_m3", rc)
+    return M3
+
+
+def lda_sketch_m3(indptr, idx, cnt, V: int, W: torch.Tensor, alpha0: float, h: torch.Tensor,
+                  g: torch.Tensor, log2b: int):
+    """B colliding sketches of M3^(W, W, W) (Alg. 3, line 4).  Returns (M3, S [B][b])."""
+    device, D, idx, cnt = _corpus(indptr, idx, cnt, V)
+    _need(W, "W", torch.float32, device)
+    k = W.shape[1]
+    h, g = _hashes_shape(h, g)
+    _need(h, "h", torch.int32, device)
+    _need(g, "g", torch.uint8, device)
+    B = h.shape[0]
+    if h.shape != (B, 1, k):
+        raise ValueError(f"h must have shape [B][1][{k}]")
+    M3 = torch.empty((k, k, k), dtype=torch.float32, device=device)
+    S = torch.empty((B, 1 << log2b), dtype=torch.complex64, device=device)
+    rc = _lib.load().lda_sketch_m3(_ctx(device), _ptr(indptr), _ptr(idx), _ptr(cnt), D, V,
+                                   _ptr(W), k, float(alpha0), _ptr(h), _ptr(g), B, log2b,
+                                   _ptr(M3), _ptr(S))
+    _lib.check("lda_sketch_m3", rc)
+    return M3, S
+
+
+def lda_recover(W: torch.Tensor, alpha0: float, lam: torch.Tensor, Vv: torch.Tensor):
+    """Alg. 3, line 6: (alpha_hat [k] float64, mu_hat [k][V], row i = topic i)."""
+    device = W.device
+    _need(W, "W", torch.float32, device)
+    V, k = W.shape
+    _need(lam, "lam", torch.float64, device, (k,))
+    _need(Vv, "Vv", torch.float32, device, (k, k))
+    alpha = torch.empty((k,), dtype=torch.float64, device=device)
+    mu = torch.empty((k, V), dtype=torch.float32, device=device)
+    rc = _lib.load().lda_recover(_ctx(device), _ptr(W), V, k, float(alpha0), _ptr(lam), _ptr(Vv),
+                                 _ptr(alpha), _ptr(mu))
+    _lib.check("lda_recover", rc)
+    return alpha, mu
+
+
+def spectral_lda(indptr, idx, cnt, V: int, k: int, alpha0: float, Omega: torch.Tensor,
+                 U0: torch.Tensor, *, B: int, log2b: int, T: int, seed: int,
+                 power_iters: int = 2):
+    """Fast spectral LDA (Alg. 3) on the device: whitening, B colliding sketches of
+    M3^(W,W,W), Alg. 1 with initial vectors U0 [k][L][k], recovery.
+    Returns dict(alpha [k] float64, mu [k][V], lam [k] float64, V [k][k], W, sigma)."""
+    W, sigma, _ = lda_whiten(indptr, idx, cnt, V, k, alpha0, Omega, power_iters)
+    h, g = cs_hashes(seed, B, log2b, [k], W.device)
+    _, S = lda_sketch_m3(indptr, idx, cnt, V, W, alpha0, h, g, log2b)
+    res = robust_power_method(S, h, g, U0, T)
+    alpha, mu = lda_recover(W, alpha0, res["lam"], res["V"])
+    return {"alpha": alpha, "mu": mu, "lam": res["lam"], "V": res["V"], "W": W, "sigma": sigma}
