@@ -116,32 +116,41 @@ def batched_problem_specs(P: int, seed: int, n_low: int = 32, n_high: int = 256,
 def lda_corpus(V: int, k: int, D: int, seed: int, alpha: float = 0.1, beta: float = 0.01,
                mean_len: float = 200.0):
     """Synthetic LDA corpus (the generative model of App. D): topic-word distributions
-    Phi[t] ~ Dir(beta 1_V), document mixtures theta_d ~ Dir(alpha 1_k), lengths m_d ~ Poisson,
-    topic counts per document ~ Multinomial(m_d, theta_d), words of topic t ~ Cat(Phi[t]).
+    Phi[t] ~ Dir(beta 1_V), document mixtures theta_d ~ Dir(alpha 1_k), m_d ~ Poisson(mean_len)
+    tokens with topics ~ Cat(theta_d) and words of topic t ~ Cat(Phi[t]).
+    Sampled in an equivalent, vectorised form: the topic counts of a document are independent
+    Poisson(mean_len theta_dt) (so m_d ~ Poisson(mean_len) and, given m_d, the counts are
+    multinomial); the words of all tokens of topic t are one multinomial draw of their total,
+    randomly permuted over those tokens.
     Returns dict(indptr int64 [D+1], idx int32 [nnz], cnt int32 [nnz], Phi [k][V], alpha [k],
-    lengths [D]) with each document's words sorted and counted (CSR)."""
+    lengths [D], ...) with each document's distinct words sorted and counted (CSR)."""
     r = rng(seed)
     Phi = r.dirichlet(np.full(V, beta), size=k)
     alpha_vec = np.full(k, alpha)
     theta = r.dirichlet(alpha_vec, size=D)
-    lengths = r.poisson(mean_len, size=D).astype(np.int64)
-    topic_counts = r.multinomial(lengths, theta)                     # D x k
-    doc_of, word_of = [], []
+    tc = r.poisson(mean_len * theta)                                 # D x k topic counts
+    lengths = tc.sum(1).astype(np.int64)
+    doc_ids = np.arange(D, dtype=np.int64)
+    keys = []
     for t in range(k):
-        ct = topic_counts[:, t]
+        ct = tc[:, t]
         tot = int(ct.sum())
         if tot == 0:
             continue
-        doc_of.append(np.repeat(np.arange(D, dtype=np.int64), ct))
-        word_of.append(r.choice(V, size=tot, p=Phi[t]).astype(np.int64))
-    doc_of = np.concatenate(doc_of)
-    word_of = np.concatenate(word_of)
-    keys, cnt = np.unique(doc_of * V + word_of, return_counts=True)
-    docs = keys // V
+        w = np.repeat(np.arange(V, dtype=np.int64), r.multinomial(tot, Phi[t]))
+        r.shuffle(w)
+        keys.append(np.repeat(doc_ids, ct) * V + w)                # (document, word) of each token
+    keys = np.sort(np.concatenate(keys)) if keys else np.zeros(0, dtype=np.int64)
+    if keys.size:
+        first = np.concatenate([[True], keys[1:] != keys[:-1]])
+        uk = keys[first]
+        cnt = np.diff(np.concatenate([np.nonzero(first)[0], [keys.size]]))
+    else:
+        uk = keys
+        cnt = np.zeros(0, dtype=np.int64)
     indptr = np.zeros(D + 1, dtype=np.int64)
-    np.add.at(indptr, docs + 1, 1)
-    indptr = np.cumsum(indptr)
-    return {"indptr": indptr, "idx": (keys % V).astype(np.int32), "cnt": cnt.astype(np.int32),
+    indptr[1:] = np.cumsum(np.bincount(uk // V, minlength=D))
+    return {"indptr": indptr, "idx": (uk % V).astype(np.int32), "cnt": cnt.astype(np.int32),
             "Phi": Phi, "alpha": alpha_vec, "lengths": lengths, "V": V, "k": k, "D": D}
 
 
