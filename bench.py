@@ -307,7 +307,7 @@ def run_ours(args):
                          f"FFT engine, random sketch values) in {el:.1f} s",
                "host_cpus": os.cpu_count()}
 
-    launches_per_step = 3 + k * (T_it + 2)
+    launches_per_step = 2 + tsk.robust_power_method_launches(B, log2b, n, k, L, T_it, dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": per_step_ms, "higher_is_better": True,
@@ -413,10 +413,10 @@ LDA_WORKLOAD = ("synthetic LDA corpus V=50000, k=100 topics, topic-word Dir(0.01
                 "M3(W,W,W), b=2^14; Alg. 1 with L=50, T=30; recovery of alpha and topics")
 
 
-def lda_launches(k: int, T: int, q: int) -> int:
+def lda_launches(rpm_launches: int, q: int) -> int:
     """Kernels of one spectral_lda call: whitening 10 + 15 (q + 1), hashes 1, whitened M3 9,
-    sketch build 1, Alg. 1 3 + k (T + 2), recovery 5."""
-    return 10 + 15 * (q + 1) + 1 + 9 + 1 + 3 + k * (T + 2) + 5
+    sketch build 1, Alg. 1 (robust_power_method_launches), recovery 5."""
+    return 10 + 15 * (q + 1) + 1 + 9 + 1 + rpm_launches + 5
 
 
 def oracle_lda_doc_rate(c, W, budget_s: float):
@@ -545,11 +545,134 @@ def run_lda(args):
             "e2e": {"value": D / e2e_s, "unit": "documents/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "s_per_step": e2e_s},
             "cpu_baseline": cpu, "clocks": clk.summary(),
-            "gpu_launches": lda_launches(k, T_it, cfg["power_iters"]) * args.steps,
+            "gpu_launches": lda_launches(tsk.robust_power_method_launches(B, log2b, k, k, L, T_it, dev),
+                                         cfg["power_iters"]) * args.steps,
             "results": {"lambda_head": [round(float(x), 4) for x in res["lam"][:5].cpu()],
                         "alpha_median": float(res["alpha"].median()),
                         "topic_l1_error_median": float(np.median(err)),
                         "topic_l1_error_max": float(err.max())}}
+    print(json.dumps(line), flush=True)
+
+
+CP_CFG = dict(dims=(500, 400, 300), R=30, B=8, log2b=15, noise=0.01, seed=4)
+CP_WORKLOAD = ("asymmetric FP32 tensor 500x400x300 (240 MB), rank 30, factor rows N(0,1) "
+               "normalised, weights U[0.5,2], noise 0.01; independent hashes per mode, B=8, "
+               "b=2^15; one step = sketched CP loss + hand-written adjoint (all factor gradients)")
+
+
+def cp_inputs(dev):
+    import torch
+    import synth
+    import paper_1506_04448_gb300 as tsk
+    c = CP_CFG
+    T, w, F0 = synth.planted_cp(c["dims"], c["R"], c["noise"], c["seed"])
+    T_d = torch.from_numpy(T).to(dev)
+    h, g = tsk.cs_hashes(c["seed"], c["B"], c["log2b"], list(c["dims"]), dev)
+    r = np.random.default_rng(c["seed"] + 1)
+    start = [torch.from_numpy(r.uniform(0.5, 2.0, c["R"]).astype(np.float32)).to(dev)]
+    for d in c["dims"]:
+        f = r.standard_normal((c["R"], d))
+        start.append(torch.from_numpy((f / np.linalg.norm(f, axis=1, keepdims=True)).astype(np.float32)).to(dev))
+    return T, T_d, h, g, start
+
+
+def run_cp(args):
+    """Sketched CP fitting (the differentiable pattern): value = loss + gradient evaluations per
+    second (forward sketches of all R rank-1 terms, residual, and the adjoint for every factor)."""
+    import torch
+    import paper_1506_04448_gb300 as tsk
+    dev = torch.device("cuda:0")
+    c = CP_CFG
+    T, T_d, h, g, start = cp_inputs(dev)
+    S = tsk.sketch_tensor(T_d, h, g, c["log2b"])
+    Xh = tsk.sketch_rfft(S)
+    dims = c["dims"]
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return tsk.cp_sketch_loss(Xh, h, g, dims, *start, with_grad=True)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(args.steps, 20)
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(reps):
+            out = step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    t_ms = e0.elapsed_time(e1) / reps
+    tsk.check_status(dev)
+    # ALS update of all three factors (Alg. 2 with the Eq. 15 Gram solve)
+    factors = [t.clone() for t in start[1:]]
+    tsk.cp_als_step(Xh, h, g, dims, factors)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(5):
+        tsk.cp_als_step(Xh, h, g, dims, factors)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    als_ms = e0.elapsed_time(e1) / 5
+    # asymmetric sketch build: the 240 MB tensor read once, after an L2 flush
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    bt = []
+    for _ in range(6):
+        flush.fill_(1.0)
+        e0.record(stream)
+        tsk.sketch_tensor(T_d, h, g, c["log2b"])
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        bt.append(e0.elapsed_time(e1))
+    b_ms = statistics.median(bt[1:])
+    pk, pk_kind = peaks()
+    b = 1 << c["log2b"]
+    build_bytes = T.nbytes + c["B"] * sum(dims) * 5 + c["B"] * b * 8
+    build_gbs = build_bytes / (b_ms / 1e3) / 1e9
+    # end to end: tensor from pinned host memory, sketch, loss + gradients back to the host
+    T_pin = torch.from_numpy(T).pin_memory()
+    def e2e_step():
+        Td = T_pin.to(dev, non_blocking=True)
+        Xh2 = tsk.sketch_rfft(tsk.sketch_tensor(Td, h, g, c["log2b"]))
+        res = tsk.cp_sketch_loss(Xh2, h, g, dims, *start, with_grad=True)
+        return [t.cpu() for t in res]
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        outs = e2e_step()
+    e2e_s = (time.perf_counter() - t0) / 3
+    d2h = sum(t.numel() * t.element_size() for t in outs)
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle as O
+        Sg = S.cpu().numpy().real.astype(np.float64)
+        hn, gn = O.cs_hashes(c["seed"], c["B"], c["log2b"], list(dims))
+        params = [t.cpu().double().numpy() for t in start]
+        t0 = time.perf_counter()
+        done = 0
+        while time.perf_counter() - t0 < args.cpu_seconds:
+            O.cp_sketch_grad(Sg, hn, gn, b, *params)
+            done += 1
+        el = time.perf_counter() - t0
+        cpu = {"value": done / el, "unit": "loss+gradient evaluations/s", "cores": 1,
+               "kind": "oracle", "sample": f"{done} oracle loss+gradient evaluations (numpy FP64 "
+                                            f"FFT engine) in {el:.1f} s", "host_cpus": os.cpu_count()}
+    line = {"metric": "sketched CP loss + adjoint gradient evaluations/s, 1 GB300",
+            "value": 1e3 / t_ms, "unit": "loss+gradient evaluations/s", "n_gpus": 1,
+            "steps": reps, "warmup": max(3, args.warmup), "ms_per_step": t_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": CP_WORKLOAD,
+                                            "l2": "sketch build timed after an L2 flush"},
+            "als_step_ms": als_ms, "loss": float(out[0]),
+            "sketch_build": {"bound": "hbm", "achieved": build_gbs, "peak": pk["hbm_gbs"],
+                             "unit": "GB/s", "frac": build_gbs / pk["hbm_gbs"], "launch_ms": b_ms,
+                             "bytes": build_bytes, "peak_kind": pk_kind},
+            "e2e": {"value": 1.0 / e2e_s, "unit": "loss+gradient evaluations/s",
+                    "h2d_bytes_per_step": T.nbytes, "d2h_bytes_per_step": d2h,
+                    "s_per_step": e2e_s, "includes": "tensor upload, sketch build, rfft, loss+grad"},
+            "cpu_baseline": cpu, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 
@@ -558,10 +681,21 @@ def run_profile(args):
     'contract' -- 6 launches of the fused contraction kernel in the power-step shape (B x L);
     'build'    -- 4 launches of the symmetric sketch build on the n = 400 tensor;
     'rtpm'     -- 2 full steps (hashes, build, Alg. 1), the first one a warm-up;
-    'lda'      -- 2 spectral_lda steps on a D = 1e5 corpus (otherwise the LDA workload)."""
+    'lda'      -- 2 spectral_lda steps on a D = 1e5 corpus (otherwise the LDA workload);
+    'cp'       -- asymmetric build + rfft, then 3 CP loss + adjoint evaluations (cfg of run_cp)."""
     import torch
     import paper_1506_04448_gb300 as tsk
     dev = torch.device("cuda:0")
+    if args.profile == "cp":
+        c = CP_CFG
+        T, T_d, h, g, start = cp_inputs(dev)
+        Xh = tsk.sketch_rfft(tsk.sketch_tensor(T_d, h, g, c["log2b"]))
+        for _ in range(3):
+            tsk.cp_sketch_loss(Xh, h, g, c["dims"], *start, with_grad=True)
+        torch.cuda.synchronize(dev)
+        tsk.check_status(dev)
+        print("profile cp done")
+        return
     if args.profile == "lda":
         import synth
         lc = dict(LDA_CFG, D=100000)
@@ -605,8 +739,8 @@ def run_profile(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile", choices=["contract", "build", "rtpm", "lda"], default=None)
-    ap.add_argument("--workload", choices=["decompose", "batched", "lda"], default="decompose")
+    ap.add_argument("--profile", choices=["contract", "build", "rtpm", "lda", "cp"], default=None)
+    ap.add_argument("--workload", choices=["decompose", "batched", "lda", "cp"], default="decompose")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -620,6 +754,8 @@ def main():
         run_batched(args)
     elif args.workload == "lda":
         run_lda(args)
+    elif args.workload == "cp":
+        run_cp(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

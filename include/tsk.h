@@ -281,6 +281,12 @@ int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* h, const ui
                         double* lambda, float* Vout, int32_t* tau_star, float* S_deflated,
                         float* lam_all, float* U_iters);
 
+/* Number of kernel launches robust_power_method makes for these sizes on ctx's device (one
+ * batched DFT, then per round G groups x (T power steps + 1 selection) + 1 deflation, where G
+ * is the number of helper-stream groups the L chains are split into).  -1 on bad sizes. */
+int64_t robust_power_method_launches(tsk_ctx* ctx, int B, int log2b, int64_t n, int k, int L,
+                                     int T);
+
 /* ---------------------------------------------------------------- many independent problems */
 
 /* One decomposition of a batch (all pointers device memory; see robust_power_method). */

@@ -10,8 +10,8 @@ lda_m2_apply, lda_whiten, lda_whitened_m3, lda_sketch_m3, lda_recover, spectral_
 """
 from .api import (cs_hashes, sketch_tensor, sketch_fft, sketch_rank1,  # noqa: F401
                   contract_iuu, contract_uuu, robust_power_method, decompose_symmetric,
-                  ctx_status, check_status, sketch_rfft, contract_ivw, cp_sketch_loss,
-                  CPSketchLoss, cp_loss, cp_als_solve, cp_als_step, BatchPlan,
-                  lda_m2_apply, lda_whiten, lda_whitened_m3, lda_sketch_m3, lda_recover,
-                  spectral_lda)
+                  robust_power_method_launches, ctx_status, check_status, sketch_rfft,
+                  contract_ivw, cp_sketch_loss, CPSketchLoss, cp_loss, cp_als_solve, cp_als_step,
+                  BatchPlan, lda_m2_apply, lda_whiten, lda_whitened_m3, lda_sketch_m3,
+                  lda_recover, spectral_lda)
 from ._lib import TskError, LIB_PATH, load as load_library  # noqa: F401

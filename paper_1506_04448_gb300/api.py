@@ -268,6 +268,13 @@ def robust_power_method(S: torch.Tensor, h: torch.Tensor, g: torch.Tensor, U0: t
     return out
 
 
+def robust_power_method_launches(B: int, log2b: int, n: int, k: int, L: int, T: int,
+                                 device="cuda") -> int:
+    """Kernel launches one robust_power_method call makes for these sizes on `device`."""
+    device = torch.device(device)
+    return int(_lib.load().robust_power_method_launches(_ctx(device), B, log2b, n, k, L, T))
+
+
 # ------------------------------------------------------------------ end-to-end call
 def decompose_symmetric(T, k: int, L: int, T_iters: int, B: int, log2b: int, seed: int,
                         U0, device="cuda"):

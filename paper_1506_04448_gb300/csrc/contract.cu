@@ -162,6 +162,28 @@ extern "C" int contract_uuu(tsk_ctx* ctx, const float* FS, const float* S, const
   return launch_contract(log2b, MODE_UUU, a, ctx->stream);
 }
 
+// The L power-iteration chains are independent until the selection, so they are split into
+// G groups, each enqueued on its own stream: while one group's step finishes its last wave of
+// blocks, the other groups' steps fill the idle SMs (a single B x L grid per step would leave
+// the SMs partly idle at the end of every step).
+static long long rpm_groups(const tsk_ctx* ctx, int B, int log2b, int L) {
+  const int per_sm = contract_blocks_per_sm(log2b);
+  const long long wave = (long long)ctx->num_sms * per_sm;
+  long long G = ((long long)L * B + wave - 1) / wave + 1;
+  if (G > L) G = L;
+  if (G > kCtxAuxStreams) G = kCtxAuxStreams;
+  return G;
+}
+
+extern "C" int64_t robust_power_method_launches(tsk_ctx* ctx, int B, int log2b, int64_t n, int k,
+                                                int L, int T) {
+  (void)n;
+  if (!ctx || k < 0 || B < 1 || L < 1 || T < 1 || log2b < 8 || log2b > 14) return -1;
+  if (k == 0) return 0;
+  const long long G = rpm_groups(ctx, B, log2b, L);
+  return 1 + (int64_t)k * (G * (T + 1) + 1);
+}
+
 extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* h,
                                    const uint8_t* g, int B, int log2b, int64_t n, int k, int L,
                                    int T, const float* U0, double* lambda, float* Vout,
@@ -185,14 +207,7 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
                       ws_round((size_t)k * L * 4) + ws_round((size_t)L * 4);
   int rc = tsk_ws_reserve(ctx, need);
   if (rc != TSK_OK) return rc;
-  // The L power-iteration chains are independent until the selection, so they are split into
-  // G groups, each enqueued on its own stream: while one group's step finishes its last wave
-  // of blocks, the other groups' steps fill the idle SMs (a single B x L grid per step would
-  // leave the SMs partly idle at the end of every step).
-  const int per_sm = contract_blocks_per_sm(log2b);
-  long long G = ((long long)L * B + (long long)ctx->num_sms * per_sm - 1) / ((long long)ctx->num_sms * per_sm) + 1;
-  if (G > L) G = L;
-  if (G > kCtxAuxStreams) G = kCtxAuxStreams;
+  const long long G = rpm_groups(ctx, B, log2b, L);
   if ((rc = tsk_ctx_aux_streams(ctx, (int)G)) != TSK_OK) return rc;
   WsCarve wc{static_cast<char*>(ctx->ws), 0};
   float2* Sw = wc.take<float2>(B * b);

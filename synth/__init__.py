@@ -154,6 +154,19 @@ def lda_corpus(V: int, k: int, D: int, seed: int, alpha: float = 0.1, beta: floa
             "Phi": Phi, "alpha": alpha_vec, "lengths": lengths, "V": V, "k": k, "D": D}
 
 
+def planted_cp(dims, R: int, noise: float, seed: int, dtype=np.float32):
+    """Asymmetric rank-R tensor sum_r w_r a_r (x) b_r (x) c_r + noise: factor rows N(0, 1)
+    normalised to unit length, weights U[0.5, 2], i.i.d. Gaussian noise of std `noise`.
+    Returns (T [dims], w [R], [A [R][n1], B [R][n2], C [R][n3]])."""
+    r = rng(seed)
+    F0 = [r.standard_normal((R, d)) for d in dims]
+    F0 = [f / np.linalg.norm(f, axis=1, keepdims=True) for f in F0]
+    w = r.uniform(0.5, 2.0, R)
+    T = np.einsum("r,ri,rj,rk->ijk", w, *F0).astype(dtype)
+    T += (noise * r.standard_normal(tuple(dims))).astype(dtype)
+    return T, w, F0
+
+
 def gaussian_matrix(rows: int, cols: int, seed: int) -> np.ndarray:
     """Standard Gaussian test matrix (the random start of a randomized range finder)."""
     return rng(seed).standard_normal((rows, cols))

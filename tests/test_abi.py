@@ -64,3 +64,7 @@ def test_binding_fails_loudly_when_library_missing(monkeypatch):
     monkeypatch.setattr(_lib, "LIB_PATH", os.path.join(ROOT, "does-not-exist", "libtsk.so"))
     with pytest.raises(RuntimeError, match="missing"):
         _lib.load()
+
+
+def test_launch_count_query_rejects_a_null_context(lib):
+    assert lib.robust_power_method_launches(None, 10, 14, 400, 20, 50, 30) == -1

@@ -144,12 +144,7 @@ CFG4 = dict(dims=(500, 400, 300), R=30, B=8, log2b=15, noise=0.01, seed=4)
 @pytest.fixture(scope="module")
 def cfg4(dev):
     c = CFG4
-    r = synth.rng(c["seed"])
-    F0 = [r.standard_normal((c["R"], d)) for d in c["dims"]]
-    F0 = [f / np.linalg.norm(f, axis=1, keepdims=True) for f in F0]
-    w = r.uniform(0.5, 2.0, c["R"])
-    T = np.einsum("r,ri,rj,rk->ijk", w, *F0).astype(np.float32)
-    T += (c["noise"] * r.standard_normal(c["dims"])).astype(np.float32)
+    T, w, F0 = synth.planted_cp(c["dims"], c["R"], c["noise"], c["seed"])
     h, g = tsk.cs_hashes(c["seed"], c["B"], c["log2b"], list(c["dims"]), dev)
     S = tsk.sketch_tensor(torch.from_numpy(T).to(dev), h, g, c["log2b"])
     Xh = tsk.sketch_rfft(S)
