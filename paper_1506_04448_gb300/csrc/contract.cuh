@@ -99,9 +99,8 @@ __device__ __forceinline__ float contract_one(float2* A, float2* Eb, float* red,
   }
   __syncthreads();
 
-  // 2. forward DFTs.
-  block_fft<LOGB, NT, -1>(A, tw);
-  block_fft<LOGB - 1, NT, -1>(Eb, tw);
+  // 2. forward DFTs (the two transforms' passes interleaved).
+  block_fft_pair<LOGB, LOGB - 1, NT, -1>(A, Eb, tw);
 
   float lam = 0.f;
   if constexpr (MODE == MODE_IUU) {
@@ -118,8 +117,7 @@ __device__ __forceinline__ float contract_one(float2* A, float2* Eb, float* red,
     }
     __syncthreads();
     // 4. inverse DFTs and hashed read-off.
-    block_fft<LOGB, NT, +1>(A, tw);
-    block_fft<LOGB - 1, NT, +1>(Eb, tw);
+    block_fft_pair<LOGB, LOGB - 1, NT, +1>(A, Eb, tw);
     for (int i = tid; i < n; i += NT) {
       const float x = __ldcg(u + i) * uscale;
       const int hi = hm[i] & (b - 1);

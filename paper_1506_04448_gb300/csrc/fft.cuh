@@ -189,6 +189,51 @@ struct FftPasses {
   }
 };
 
+// Two independent in-place transforms (NA points at xa, NE points at xe, same direction) whose
+// passes are interleaved: step p runs pass p of A (load, sync, store) and then pass p of E
+// (load, sync, store).  E's barrier also orders A's stores before A's next loads, and A's next
+// barrier orders E's stores before E's next loads, so a step costs two barriers where the two
+// transforms run one after the other would cost four.  An extra barrier is taken only when a
+// step lacks one of the two parts.  PREV_E: the previous step ended with an E part.
+template <int NA, int NE, int NT, int NSA, int NSE, int DIR, bool PREV_E = true>
+struct FftPair {
+  static constexpr int EA = NA / NT, EE = NE / NT;
+  static constexpr int RMA = EA > 16 ? 16 : EA, RME = EE > 16 ? 16 : EE;
+  static constexpr bool DO_A = NSA < NA, DO_E = NSE < NE;
+  static constexpr int RA = !DO_A ? 1 : (NA / NSA >= RMA ? RMA : NA / NSA);
+  static constexpr int RE = !DO_E ? 1 : (NE / NSE >= RME ? RME : NE / NSE);
+  static __device__ __forceinline__ void run(float2* xa, float2* xe, const float2* tw) {
+    if constexpr (DO_A) {
+      if constexpr (!PREV_E) __syncthreads();
+      float2 v[EA];
+      StockhamPass<NA, NT, RA, NSA, DIR>::load_compute(xa, tw, threadIdx.x, v);
+      __syncthreads();
+      StockhamPass<NA, NT, RA, NSA, DIR>::store(xa, threadIdx.x, v);
+    }
+    if constexpr (DO_E) {
+      if constexpr (!DO_A) __syncthreads();
+      float2 w[EE];
+      StockhamPass<NE, NT, RE, NSE, DIR>::load_compute(xe, tw, threadIdx.x, w);
+      __syncthreads();
+      StockhamPass<NE, NT, RE, NSE, DIR>::store(xe, threadIdx.x, w);
+    }
+    if constexpr (DO_A || DO_E) {
+      FftPair<NA, NE, NT, NSA * RA, NSE * RE, DIR, DO_E>::run(xa, xe, tw);
+    } else {
+      __syncthreads();
+    }
+  }
+};
+
+// block_fft of two arrays at once (xa: 2^LOGA points, xe: 2^LOGE points), interleaved as above.
+template <int LOGA, int LOGE, int NT, int DIR>
+__device__ __forceinline__ void block_fft_pair(float2* xa, float2* xe, const float2* tw) {
+  constexpr int NA = 1 << LOGA, NE = 1 << LOGE;
+  static_assert(NA / NT >= 2 && NA / NT <= 32 && NE / NT >= 2 && NE / NT <= 32, "2..32 per thread");
+  static_assert(LOGA <= kTwLog && LOGE <= kTwLog, "twiddle table covers transforms up to 2^15");
+  FftPair<NA, NE, NT, 1, 1, DIR>::run(xa, xe, tw);
+}
+
 // In-place FFT of N = 2^LOGN complex values at x (padded layout) by a block of exactly NT
 // threads, with the twiddle table tw (fill_twiddles).  Must be called by all NT threads;
 // begins and ends with the data synchronised.
