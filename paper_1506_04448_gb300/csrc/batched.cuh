@@ -33,7 +33,8 @@ struct BatchProblem {            // device-side descriptor of one problem
 
 // Power step t (MODE_IUU) or selection (MODE_UUU) of round r; grid (B, L, active problems).
 template <int LOGB, int MODE, int NT>
-__global__ void __launch_bounds__(NT, 1) batch_contract_kernel(const BatchProblem* probs, int B,
+__global__ void __launch_bounds__(NT, contract_min_blocks(LOGB, NT))
+    batch_contract_kernel(const BatchProblem* probs, int B,
                                                                int L, int T, int t, int r,
                                                                int* status) {
   constexpr int b = 1 << LOGB;
@@ -60,7 +61,8 @@ __global__ void __launch_bounds__(NT, 1) batch_contract_kernel(const BatchProble
   if (!arrive_is_last(&P.counters[tau], (unsigned)B, &s_last)) return;
   if constexpr (MODE == MODE_IUU) {
     float* un = P.Ubuf + ((size_t)((t + 1) & 1) * L + tau) * n;
-    median_vector<NT>(P.Vall + (size_t)tau * B * n, B, n, un, un, red, status);
+    median_vector<NT>(P.Vall + (size_t)tau * B * n, B, n, un, un, red, status,
+                      reinterpret_cast<float*>(A), 2 * (padded_len(b) + padded_len(b / 2)));
     if (P.U_iters) {
       float* tr = P.U_iters + (((size_t)r * T + t) * L + tau) * n;
       for (int i = threadIdx.x; i < n; i += NT) tr[i] = un[i];

@@ -166,28 +166,39 @@ __device__ __forceinline__ bool arrive_is_last(unsigned* counter, unsigned group
 }
 
 // Median over the B sketches of every entry of one vector (Vt: [B][n]) into dst; if unext is
-// given, dst / ||dst|| is written there (dst may equal unext).  Called by the last block.
+// given, dst / ||dst|| is written there (dst may equal unext).  Called by the last block, with
+// `scratch` a shared-memory area of scratch_floats >= B floats that the block no longer needs
+// (its FFT buffers): each taking part thread sorts its B values in a column of it (entry c at
+// scratch[c * P + t], P threads taking part), not in a per-thread local-memory array, whose
+// traffic would go to L2 when shared memory leaves little L1.  Ends synchronised.
 template <int NT>
 __device__ __forceinline__ void median_vector(const float* Vt, int B, int n, float* dst,
-                                              float* unext, float* red, int* status) {
+                                              float* unext, float* red, int* status,
+                                              float* scratch, int scratch_floats) {
+  const int P = min(NT, scratch_floats / B);
+  const int t = threadIdx.x;
   float ss = 0.f;
-  for (int i = threadIdx.x; i < n; i += NT) {
-    float vals[kMaxB];
-    for (int c = 0; c < B; ++c) vals[c] = __ldcg(Vt + (size_t)c * n + i);
-    const float med = small_median(vals, B);
-    dst[i] = med;
-    ss += med * med;
+  if (t < P) {
+    float* x = scratch + t;
+    for (int i = t; i < n; i += P) {
+      for (int c = 0; c < B; ++c) x[c * P] = __ldcg(Vt + (size_t)c * n + i);
+      const float med = small_median_strided(x, B, P);
+      dst[i] = med;
+      ss += med * med;
+    }
   }
   if (unext) {
     ss = block_sum<NT>(ss, red);
     float inv = 0.f;
     if (!(ss > 0.f) || !isfinite(ss)) {
-      if (threadIdx.x == 0) tsk_set_status(status, TSK_ENONFINITE);
+      if (t == 0) tsk_set_status(status, TSK_ENONFINITE);
     } else {
       inv = 1.f / sqrtf(ss);
     }
-    for (int i = threadIdx.x; i < n; i += NT) unext[i] = dst[i] * inv;
+    if (t < P)
+      for (int i = t; i < n; i += P) unext[i] = dst[i] * inv;
   }
+  __syncthreads();
 }
 
 __device__ __forceinline__ float median_of(const float* x, int B) {
@@ -244,7 +255,9 @@ __device__ __forceinline__ int first_argmax(const float* x, int L) {
 // ------------------------------------------------------------------ single-step kernels
 
 template <int LOGB, int MODE>
-__global__ void __launch_bounds__(threads_for_logb(LOGB), 1) contract_kernel(ContractArgs a) {
+__global__ void __launch_bounds__(threads_for_logb(LOGB),
+                                  contract_min_blocks(LOGB, threads_for_logb(LOGB)))
+    contract_kernel(ContractArgs a) {
   constexpr int NT = threads_for_logb(LOGB);
   constexpr int b = 1 << LOGB;
   extern __shared__ float2 smem[];
@@ -269,7 +282,8 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB), 1) contract_kernel(Con
     if (a.Vmed == nullptr && a.Unext == nullptr) return;
     float* dst = a.Vmed ? a.Vmed + (size_t)tau * n : a.Unext + (size_t)tau * n;
     median_vector<NT>(a.Vall + (size_t)tau * B * n, B, n, dst,
-                      a.Unext ? a.Unext + (size_t)tau * n : nullptr, red, a.status);
+                      a.Unext ? a.Unext + (size_t)tau * n : nullptr, red, a.status,
+                      reinterpret_cast<float*>(A), 2 * (padded_len(b) + padded_len(b / 2)));
   }
 }
 

@@ -318,6 +318,15 @@ __device__ __forceinline__ float& real_at(float2* x, int k) {
   return reinterpret_cast<float*>(&x[pad_idx(k >> 1)])[k & 1];
 }
 
+// Resident blocks per SM that the contraction kernels ask the compiler to fit.  With 16 elements
+// per thread, 1024 threads per SM (64 registers per thread) fit without spills, and shared
+// memory (about 12.75 b bytes per block) allows that many blocks for every b.  One-warp blocks
+// (b <= 2^9) ask for half as many, and blocks with 32 elements per thread for one (they need
+// more than 128 registers per thread).
+constexpr int contract_min_blocks(int logb, int nt) {
+  return (1 << logb) / nt > 16 ? 1 : (nt <= 32 ? 16 : 1024 / nt);
+}
+
 // Threads per block used by the sketch-length-b kernels: b/16 (one radix-16 butterfly, 16
 // elements, per thread and pass of a length-b transform), at least one warp, at most 1024.
 constexpr int threads_for_logb(int logb) {

@@ -45,4 +45,20 @@ __device__ __forceinline__ float small_median(float* x, int cnt) {
   return (cnt & 1) ? x[cnt / 2] : 0.5f * (x[cnt / 2 - 1] + x[cnt / 2]);
 }
 
+// small_median on cnt values spaced `stride` apart (a column of a shared-memory scratch array,
+// so that the threads of a warp sort in different banks).
+__device__ __forceinline__ float small_median_strided(float* x, int cnt, int stride) {
+  for (int a = 1; a < cnt; ++a) {
+    const float key = x[a * stride];
+    int c = a - 1;
+    while (c >= 0 && x[c * stride] > key) {
+      x[(c + 1) * stride] = x[c * stride];
+      --c;
+    }
+    x[(c + 1) * stride] = key;
+  }
+  const int h = cnt / 2;
+  return (cnt & 1) ? x[h * stride] : 0.5f * (x[(h - 1) * stride] + x[h * stride]);
+}
+
 }  // namespace tsk

@@ -68,6 +68,28 @@ def planted_symmetric(n: int, k: int, noise: float, seed: int,
     return T.astype(dtype, copy=False), lam, A
 
 
+def paper_synthetic(n: int, sigma: float, seed: int):
+    """The synthetic tensor of the paper's experiments (Sec. 5.1): T = S / ||S||_F + E with
+    S = sum_{i<=n} lam_i v_i (x) v_i (x) v_i, lam_i = 1/i, v_i the orthonormal columns of V (full
+    rank), and E symmetric with one N(0, (sigma / n^1.5)^2) draw per i <= j <= k.  Float32, built
+    one slice T[i] at a time (n = 1000 is 4 GB).  Returns (T, lam_normalised, V)."""
+    lam = 1.0 / np.arange(1, n + 1, dtype=np.float64)
+    lam /= np.linalg.norm(lam)                     # ||S||_F = ||lam||_2 for orthonormal v_i
+    V = orthonormal_columns(n, n, seed + 1)
+    std = sigma / n ** 1.5
+    g = rng(seed + 2).standard_normal((n, n, n), dtype=np.float32)
+    T = np.empty((n, n, n), dtype=np.float32)
+    jj, kk = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    for i in range(n):
+        ii = np.full_like(jj, i)
+        lo = np.minimum(np.minimum(ii, jj), kk)
+        hi = np.maximum(np.maximum(ii, jj), kk)
+        mid = ii + jj + kk - lo - hi
+        sig_i = (V * (lam * V[i])[None, :]) @ V.T
+        T[i] = (sig_i + std * g[lo, mid, hi].astype(np.float64)).astype(np.float32)
+    return T, lam, V
+
+
 def random_symmetric(n: int, seed: int, dtype=np.float64) -> np.ndarray:
     """Dense symmetric tensor with N(0,1) independent entries (i <= j <= k)."""
     return symmetric_noise(n, 1.0, seed, dtype=dtype)

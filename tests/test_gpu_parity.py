@@ -166,7 +166,8 @@ def _sketches(dev, n, log2b, B, seed, noise=0.1, k=3):
 
 
 @pytest.mark.parametrize("n,log2b,B,L", [(5, 8, 1, 1), (37, 10, 2, 3), (64, 12, 5, 2),
-                                         (33, 13, 4, 2), (400, 14, 10, 3)])
+                                         (33, 13, 4, 2), (400, 14, 10, 3),
+                                         (20, 9, 40, 2), (12, 8, 64, 2)])   # medians of 40, 64
 def test_contract_iuu_and_uuu(dev, n, log2b, B, L):
     b = 1 << log2b
     _, h, g, S, FS, ho, go = _sketches(dev, n, log2b, B, 31 + n)
@@ -232,7 +233,8 @@ def _run_rtpm(dev, n, k, L, T_it, B, log2b, seed, noise):
 @pytest.mark.parametrize("n,k,L,T_it,B,log2b,noise", [
     (50, 5, 10, 20, 5, 10, 0.01),     # the small planted configuration
     (37, 3, 4, 6, 4, 9, 0.1),         # ragged n, even B
-    (16, 2, 3, 5, 1, 8, 0.05)])       # a single sketch (median of one)
+    (16, 2, 3, 5, 1, 8, 0.05),        # a single sketch (median of one)
+    (24, 2, 3, 4, 40, 10, 0.01)])     # B = 40 as in the paper's largest sketch count
 def test_rtpm_stepwise_parity(dev, n, k, L, T_it, B, log2b, noise):
     from rtpm_check import check_rtpm_stepwise
     res, Sg, ho, go, U0g, _, _ = _run_rtpm(dev, n, k, L, T_it, B, log2b, 1, noise)
