@@ -59,31 +59,6 @@ int launch_deflate(int log2b, const DeflateArgs& a, int B, cudaStream_t st) {
   }
 }
 
-template <int LOGB>
-static int blocks_per_sm_t() {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, contract_kernel<LOGB, MODE_IUU>,
-                                                    threads_for_logb(LOGB),
-                                                    contract_smem_bytes<LOGB>()) != cudaSuccess) {
-    cudaGetLastError();
-    return 1;
-  }
-  return per_sm < 1 ? 1 : per_sm;
-}
-
-// Resident contraction blocks per SM at sketch length 2^log2b.
-static int contract_blocks_per_sm(int log2b) {
-  switch (log2b) {
-    case 8: return blocks_per_sm_t<8>();
-    case 9: return blocks_per_sm_t<9>();
-    case 10: return blocks_per_sm_t<10>();
-    case 11: return blocks_per_sm_t<11>();
-    case 12: return blocks_per_sm_t<12>();
-    case 13: return blocks_per_sm_t<13>();
-    default: return blocks_per_sm_t<14>();
-  }
-}
-
 int launch_fft_batched(int log2b, const float2* in, float2* out, int B, int inverse, cudaStream_t st);
 
 }  // namespace tsk
@@ -163,16 +138,12 @@ extern "C" int contract_uuu(tsk_ctx* ctx, const float* FS, const float* S, const
 }
 
 // The L power-iteration chains are independent until the selection, so they are split into
-// G groups, each enqueued on its own stream: while one group's step finishes its last wave of
-// blocks, the other groups' steps fill the idle SMs (a single B x L grid per step would leave
-// the SMs partly idle at the end of every step).
-static long long rpm_groups(const tsk_ctx* ctx, int B, int log2b, int L) {
-  const int per_sm = contract_blocks_per_sm(log2b);
-  const long long wave = (long long)ctx->num_sms * per_sm;
-  long long G = ((long long)L * B + wave - 1) / wave + 1;
-  if (G > L) G = L;
-  if (G > kCtxAuxStreams) G = kCtxAuxStreams;
-  return G;
+// G = min(L, 8) groups, each enqueued on its own stream: while one group's step finishes its
+// last wave of blocks and its last-arriving blocks take the medians, the other groups' steps
+// fill the idle SMs (a single B x L grid per step would leave the SMs partly idle at the end of
+// every step).  Eight groups measured at least as fast as fewer for every sketch length.
+static long long rpm_groups(int L) {
+  return L < kCtxAuxStreams ? L : kCtxAuxStreams;
 }
 
 extern "C" int64_t robust_power_method_launches(tsk_ctx* ctx, int B, int log2b, int64_t n, int k,
@@ -180,7 +151,7 @@ extern "C" int64_t robust_power_method_launches(tsk_ctx* ctx, int B, int log2b, 
   (void)n;
   if (!ctx || k < 0 || B < 1 || L < 1 || T < 1 || log2b < 8 || log2b > 14) return -1;
   if (k == 0) return 0;
-  const long long G = rpm_groups(ctx, B, log2b, L);
+  const long long G = rpm_groups(L);
   return 1 + (int64_t)k * (G * (T + 1) + 1);
 }
 
@@ -207,7 +178,7 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
                       ws_round((size_t)k * L * 4) + ws_round((size_t)L * 4);
   int rc = tsk_ws_reserve(ctx, need);
   if (rc != TSK_OK) return rc;
-  const long long G = rpm_groups(ctx, B, log2b, L);
+  const long long G = rpm_groups(L);
   if ((rc = tsk_ctx_aux_streams(ctx, (int)G)) != TSK_OK) return rc;
   WsCarve wc{static_cast<char*>(ctx->ws), 0};
   float2* Sw = wc.take<float2>(B * b);
