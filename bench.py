@@ -70,6 +70,25 @@ def contraction_smem_bytes(log2b: int) -> float:
     return 2 * (passes_b * 2 * 8 * b + passes_h * 2 * 8 * (b // 2)) + 4 * 8 * b
 
 
+def measured_traffic(summary: str):
+    """DRAM bytes per launch of the benchmarked kernel from its committed ncu summary, or None
+    when the kernel's sources have changed since the counters were taken."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", summary)
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"<!-- traffic: (\{.*\}) -->", open(path).read())
+    if not m:
+        return None
+    meta = json.loads(m.group(1))
+    pkg = os.path.join(ROOT, "paper_1506_04448_gb300")
+    data = b"".join(open(os.path.join(pkg, f), "rb").read() for f in meta["sources"])
+    if hashlib.sha256(data).hexdigest() != meta["sources_sha256"]:
+        return None
+    return meta["traffic_bytes_per_launch"]
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -339,7 +358,9 @@ def run_ours(args):
         "sketch_contractions_per_s": value * B,
         "roofline": {"kernel": "contract_kernel<14, MODE_IUU> (grid B x L = 10 x 50)",
                      "bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": achieved_tf / alu_peak, "traffic": None,
+                     "frac": achieved_tf / alu_peak,
+                     "traffic": measured_traffic("contract_kernel_n400_b16384.md"),
+                     "traffic_note": "DRAM bytes per launch from the ncu capture in profiles/ (null if the kernel changed since)",
                      "launch_ms": k_ms, "flops_per_launch": flops,
                      "flops_executed_per_launch": B * L * contraction_flops_executed(log2b),
                      "flops_basis": "4 length-b FFTs x 5 b log2 b per sketch-contraction",
