@@ -26,7 +26,8 @@ from .sketch import (count_sketch, count_sketch_asym, sketch_tensor_sym,  # noqa
                      sketch_rank1_sym, sketch_rank1_asym, recover_entry_sym)
 from .contract import (exact_iuu, exact_uuu, exact_ivw, contract_iuu, contract_uuu,  # noqa: F401
                        contract_iuu_def, contract_uuu_def, contract_ivw_asym)
-from .rtpm import (median, median_rows, rtpm_sketched, rtpm_exact, power_step_sketched,  # noqa: F401
+from .rtpm import (median, median_rows, rtpm_sketched, rtpm_sketched_asym, rtpm_exact,  # noqa: F401
+                   power_step_sketched,
                    eigenvalue_sketched, deflate_sketches, NonFiniteError)
 from . import cp  # noqa: F401,E402
 from .cp import (cp_sketch_loss, cp_sketch_grad, cp_exact_loss, contract_ivw_mode,  # noqa: F401,E402

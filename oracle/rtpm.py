@@ -126,3 +126,45 @@ def rtpm_exact(T: np.ndarray, U0: np.ndarray, T_iters: int, tau_choice=None):
         u = U[tau_star]
         T = T - lam[tau_star] * np.einsum("i,j,k->ijk", u, u, u)
     return {"lam": lam_out, "V": V_out, "tau": tau_out}
+
+
+def rtpm_sketched_asym(S: np.ndarray, h, g, b: int, U0: np.ndarray, T_iters: int,
+                       engine: str = "fft", tau_choice=None):
+    """Alg. 1 exactly as printed: B asymmetric sketches S[m] (Eq. 1, real, time domain) built
+    with three independent hashes h[m][j], xi[m][j] (j = 0, 1, 2 for modes 1, 2, 3).
+
+    Power update: v^(m)_i = xi_1(i) [F^-1(F s_T o conj F s_{2,u} o conj F s_{3,u})]_{h_1(i)},
+    u <- median_m Re v^(m) / ||.||.  Selection: lambda^(m)_tau = T^(m)(u,u,u), which by
+    Prop. 1's linearity is sum_i u_i v^(m)_i(u); lambda_tau = median_m, tau* = first argmax.
+    Deflation: every sketch loses lambda^ s_{1,u^} * s_{2,u^} * s_{3,u^} (Eq. 4).
+    Same readings as rtpm_sketched (median, fresh inputs U0[r][tau], no refinement)."""
+    from .contract import contract_ivw_asym
+    from .sketch import sketch_rank1_asym
+    k, L, n = U0.shape
+    B = S.shape[0]
+    S = np.array(np.real(S), dtype=np.float64, copy=True)
+    lam_out = np.zeros(k)
+    V_out = np.zeros((k, n))
+    tau_out = np.zeros(k, dtype=np.int64)
+    U_final = np.zeros((k, L, n))
+    lam_all = np.zeros((k, L))
+
+    def per_sketch(u):
+        return np.stack([contract_ivw_asym(S[m], u, u, h[m], g[m], b, n, engine) for m in range(B)])
+
+    for r in range(k):
+        U = np.stack([normalise(U0[r, tau]) for tau in range(L)])
+        for _ in range(T_iters):
+            U = np.stack([normalise(median_rows(per_sketch(U[tau]))) for tau in range(L)])
+        lam = np.array([median(per_sketch(U[tau]) @ U[tau]) for tau in range(L)])
+        tau_star = int(np.argmax(lam)) if tau_choice is None else int(tau_choice[r])
+        lam_out[r] = lam[tau_star]
+        V_out[r] = U[tau_star]
+        tau_out[r] = tau_star
+        U_final[r] = U
+        lam_all[r] = lam
+        u = U[tau_star]
+        for m in range(B):
+            S[m] = S[m] - lam[tau_star] * np.real(sketch_rank1_asym(u, u, u, h[m], g[m], b))
+    return {"lam": lam_out, "V": V_out, "tau": tau_out, "U_final": U_final,
+            "lam_all": lam_all, "S_deflated": S}

@@ -352,6 +352,27 @@ def test_sketched_rtpm_collision_free_equals_exact():
     np.testing.assert_allclose(sk["V"], ex["V"], atol=1e-9)
 
 
+def test_asymmetric_rtpm_with_injective_hashes_is_the_plain_method():
+    """Alg. 1 as printed (three hashes, Eq. 1 sketches): with h1(i) = i, h2(j) = n j,
+    h3(k) = n^2 k every (i, j, k) has its own bucket, so each T(I,u,u) read-off and each
+    deflation is exact and the method reduces to the plain one step for step."""
+    n, k = 4, 2
+    hrow = np.stack([np.arange(n), n * np.arange(n), n * n * np.arange(n)])
+    b = n ** 3
+    T, lam, A = synth.planted_symmetric(n, k, 0.05, 211)
+    Bn = 3
+    h = np.stack([hrow] * Bn)
+    g = np.stack([synth.rng(212 + m).integers(0, 4, size=(3, n)) for m in range(Bn)])
+    S = np.stack([np.real(O.sketch_tensor_asym(T, h[m], g[m], b)) for m in range(Bn)])
+    U0 = synth.gaussian_inits(k, 4, n, 213)
+    sk = O.rtpm_sketched_asym(S, h, g, b, U0, 15, engine="fft")
+    ex = O.rtpm_exact(T, U0, 15)
+    for r in range(k):
+        assert sk["lam_all"][r, sk["tau"][r]] >= sk["lam_all"][r].max() - 1e-12
+    np.testing.assert_allclose(sk["lam"], ex["lam"], rtol=1e-9)
+    np.testing.assert_allclose(sk["V"], ex["V"], atol=1e-9)
+
+
 # ------------------------------------------------------------------ sketched CP loss, ALS (Alg. 2)
 def _injective_asym(n1, n2, n3):
     """h1(i) = i, h2(j) = n1 j, h3(k) = n1 n2 k: H is injective on [n1] x [n2] x [n3]."""
