@@ -205,6 +205,23 @@ int cp_sketch_loss(tsk_ctx* ctx, const float* Xh, const int32_t* h, const uint8_
 int cp_als_solve(tsk_ctx* ctx, const float* M, const float* P, const float* Q, int K, int64_t n,
                  int64_t np, int64_t nq, float* out, float* lam);
 
+/* Alg. 1 exactly as printed: three independent hashes and B asymmetric sketches (Eq. 1) of a
+ * symmetric n x n x n tensor.  S: [B][b] TSK_C64, real parts used (sketch_tensor with M = 3,
+ * dims {n, n, n}); h, g: [B][3][n].  For r = 0..k-1 and every tau < L:
+ *   T power updates  v^(m)_i = xi_1(i) [F^-1(F s_T o conj F s_2,u o conj F s_3,u)]_{h_1(i)},
+ *                    u <- median_m Re v^(m) / ||.||;
+ *   selection        lambda^(m)_tau = sum_i u_i v^(m)_i(u) (= T^(m)(u,u,u), Prop. 1),
+ *                    lambda_tau = median_m, tau* = first argmax;
+ *   deflation        every sketch loses lambda^ s_1,u^ * s_2,u^ * s_3,u^ (Eq. 4), applied to
+ *                    the half spectra that all later contractions use.
+ * Outputs as robust_power_method: lambda [k] double, Vout [k][n], tau_star [k] (may be NULL),
+ * lam_all optional [k][L], U_iters optional [k][T][L][n].  A zero/non-finite norm is reported by
+ * tsk_ctx_status() as TSK_ENONFINITE.  Limits: log2b in [9, 15], B <= 64, n <= 8192, T >= 1. */
+int robust_power_method_asym(tsk_ctx* ctx, const float* S, const int32_t* h, const uint8_t* g,
+                             int B, int log2b, int64_t n, int k, int L, int T, const float* U0,
+                             double* lambda, float* Vout, int32_t* tau_star, float* lam_all,
+                             float* U_iters);
+
 /* ---------------------------------------------------------------- spectral LDA (App. D, Alg. 3) */
 
 /* Corpora are CSR word counts on the device: indptr int64 [D+1] (indptr[0] = 0, nondecreasing),

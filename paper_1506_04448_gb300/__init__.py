@@ -10,7 +10,7 @@ lda_m2_apply, lda_whiten, lda_whitened_m3, lda_sketch_m3, lda_recover, spectral_
 """
 from .api import (cs_hashes, sketch_tensor, sketch_fft, sketch_rank1,  # noqa: F401
                   contract_iuu, contract_uuu, robust_power_method, decompose_symmetric,
-                  robust_power_method_launches, ctx_status, check_status, sketch_rfft,
+                  robust_power_method_launches, robust_power_method_asym, ctx_status, check_status, sketch_rfft,
                   contract_ivw, cp_sketch_loss, CPSketchLoss, cp_loss, cp_als_solve, cp_als_step,
                   BatchPlan, lda_m2_apply, lda_whiten, lda_whitened_m3, lda_sketch_m3,
                   lda_recover, spectral_lda)

@@ -268,6 +268,38 @@ def robust_power_method(S: torch.Tensor, h: torch.Tensor, g: torch.Tensor, U0: t
     return out
 
 
+def robust_power_method_asym(S: torch.Tensor, h: torch.Tensor, g: torch.Tensor, U0: torch.Tensor,
+                             T: int, return_trace: bool = False):
+    """Alg. 1 as printed, on B asymmetric sketches S [B][b] (complex64, real parts used) of a
+    symmetric tensor with hashes h, g [B][3][n] and initial vectors U0 [k][L][n].
+    Returns dict(lam [k] float64, V [k][n], tau [k] int32[, lam_all [k][L], U_iters [k][T][L][n]])."""
+    device = S.device
+    _need(S, "S", torch.complex64, device)
+    B, b = S.shape
+    _need(h, "h", torch.int32, device)
+    _need(g, "g", torch.uint8, device)
+    _need(U0, "U0", torch.float32, device)
+    k, L, n = U0.shape
+    if tuple(h.shape) != (B, 3, n) or h.shape != g.shape:
+        raise ValueError(f"h and g must have shape [{B}][3][{n}]")
+    log2b = b.bit_length() - 1
+    lam = torch.empty((k,), dtype=torch.float64, device=device)
+    V = torch.empty((k, n), dtype=torch.float32, device=device)
+    tau = torch.empty((k,), dtype=torch.int32, device=device)
+    lam_all = torch.empty((k, L), dtype=torch.float32, device=device) if return_trace else None
+    U_iters = (torch.empty((k, int(T), L, n), dtype=torch.float32, device=device)
+               if return_trace else None)
+    rc = _lib.load().robust_power_method_asym(_ctx(device), _ptr(S), _ptr(h), _ptr(g), B, log2b,
+                                              n, k, L, int(T), _ptr(U0), _ptr(lam), _ptr(V),
+                                              _ptr(tau), _ptr(lam_all), _ptr(U_iters))
+    _lib.check("robust_power_method_asym", rc)
+    out = {"lam": lam, "V": V, "tau": tau}
+    if return_trace:
+        out["lam_all"] = lam_all
+        out["U_iters"] = U_iters
+    return out
+
+
 def robust_power_method_launches(B: int, log2b: int, n: int, k: int, L: int, T: int,
                                  device="cuda") -> int:
     """Kernel launches one robust_power_method call makes for these sizes on `device`."""

@@ -14,6 +14,7 @@
 namespace tsk {
 
 constexpr int kMaxRank = 64;
+constexpr int kMaxB64 = 64;
 
 template <int LOGB>
 constexpr int asym_threads() { return threads_for_logb(LOGB - 1); }
@@ -134,12 +135,119 @@ __global__ void __launch_bounds__(asym_threads<LOGB>(), 1) ivw_kernel(IvwArgs a)
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  for (int i = threadIdx.x; i < a.n_o; i += NT) {
-    float vals[64];
-    for (int c = 0; c < a.B; ++c) vals[c] = __ldcg(&a.Vall[((size_t)r * a.B + c) * a.n_o + i]);
-    a.Vmed[(size_t)r * a.n_o + i] = small_median(vals, a.B);
+  // median over the B sketches; each thread sorts its values in a column of the (now free)
+  // transform buffer rather than in a local-memory array
+  float* scratch = reinterpret_cast<float*>(X);
+  const int P = min(NT, 2 * padded_len(N) / a.B);
+  if ((int)threadIdx.x < P) {
+    float* x = scratch + threadIdx.x;
+    for (int i = threadIdx.x; i < a.n_o; i += P) {
+      for (int c = 0; c < a.B; ++c) x[c * P] = __ldcg(&a.Vall[((size_t)r * a.B + c) * a.n_o + i]);
+      a.Vmed[(size_t)r * a.n_o + i] = small_median_strided(x, a.B, P);
+    }
   }
   if (threadIdx.x == 0) a.counters[r] = 0u;
+}
+
+// ------------------------------------------------------------------ Alg. 1 as printed (three hashes)
+// Rows of `in` ([rows][n]) scaled to unit length into `out` (may alias); a zero or non-finite
+// norm is recorded as TSK_ENONFINITE and gives a zero row.  One block per row.
+__global__ void __launch_bounds__(256) normalize_rows_kernel(const float* in, float* out, int n,
+                                                             int* status) {
+  __shared__ float red[33];
+  const float* x = in + (size_t)blockIdx.x * n;
+  float ss = 0.f;
+  for (int i = threadIdx.x; i < n; i += 256) {
+    const float v = __ldcg(x + i);
+    ss += v * v;
+  }
+  ss = block_sum<256>(ss, red);
+  float inv = 0.f;
+  if (!(ss > 0.f) || !isfinite(ss)) {
+    if (threadIdx.x == 0) tsk_set_status(status, TSK_ENONFINITE);
+  } else {
+    inv = 1.f / sqrtf(ss);
+  }
+  float* y = out + (size_t)blockIdx.x * n;
+  for (int i = threadIdx.x; i < n; i += 256) y[i] = __ldcg(x + i) * inv;
+}
+
+// Selection step: lambda^(m)_tau = sum_i u_i v^(m)_i (= T^(m)(u,u,u) by the linearity of
+// Prop. 1) for every sketch m, and lam[tau] = their median.  One block per tau.
+__global__ void __launch_bounds__(256) asym_select_kernel(const float* U, const float* Vall, int B,
+                                                          int n, float* lam) {
+  __shared__ float red[33];
+  __shared__ float per[kMaxB64];
+  const int tau = blockIdx.x;
+  const float* u = U + (size_t)tau * n;
+  for (int m = 0; m < B; ++m) {
+    const float* v = Vall + ((size_t)tau * B + m) * n;
+    float d = 0.f;
+    for (int i = threadIdx.x; i < n; i += 256) d += __ldcg(u + i) * __ldcg(v + i);
+    d = block_sum<256>(d, red);
+    if (threadIdx.x == 0) per[m] = d;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) lam[tau] = small_median(per, B);
+}
+
+// tau* = first argmax of lam[0..L), then lambda[r] = lam[tau*], Vout[r] = U[tau*], tau_out[r],
+// and the deflation weight defl = lam[tau*].  One block.
+__global__ void __launch_bounds__(256) asym_pick_kernel(const float* lam, int L, const float* U,
+                                                        int n, int r, double* lambda, float* Vout,
+                                                        int32_t* tau_out, float* defl) {
+  __shared__ int s_tau;
+  if (threadIdx.x == 0) {
+    int best = 0;
+    float bv = __ldcg(lam);
+    for (int t = 1; t < L; ++t) {
+      const float v = __ldcg(lam + t);
+      if (v > bv) { bv = v; best = t; }
+    }
+    s_tau = best;
+    lambda[r] = (double)bv;
+    if (tau_out) tau_out[r] = best;
+    *defl = bv;
+  }
+  __syncthreads();
+  const float* u = U + (size_t)s_tau * n;
+  for (int i = threadIdx.x; i < n; i += 256) Vout[(size_t)r * n + i] = __ldcg(u + i);
+}
+
+// Deflation of sketch m = blockIdx.x in the frequency domain:
+//   Xh[m] -= defl * F s_1,u o F s_2,u o F s_3,u   (Eq. 4; the half spectra of the real sketches),
+// the product accumulated in dspec[m] ([B][N+1] workspace).
+template <int LOGB>
+__global__ void __launch_bounds__(asym_threads<LOGB>(), 1) asym_deflate_kernel(
+    float2* Xh, const int32_t* h, const uint8_t* g, int nmax, const float* u, int n,
+    const float* defl, float2* dspec) {
+  constexpr int NT = asym_threads<LOGB>();
+  constexpr int b = 1 << LOGB;
+  constexpr int N = b / 2;
+  extern __shared__ float2 smem[];
+  float2* X = smem;
+  float2* last = smem + padded_len(N);
+  __shared__ float2 tw[kTwEntries];
+  fill_twiddles(tw, NT);
+  const int m = blockIdx.x;
+  const int32_t* hm = h + (size_t)m * 3 * nmax;
+  const uint8_t* gm = g + (size_t)m * 3 * nmax;
+  float2* P = dspec + (size_t)m * (N + 1);
+  float2* Xm = Xh + (size_t)m * (N + 1);
+  const float lam = __ldcg(defl);
+  for (int j = 0; j < 3; ++j) {
+    zero_signal<LOGB>(X, last);
+    scatter_real<NT>(X, u, n, hm + (size_t)j * nmax, gm + (size_t)j * nmax, b - 1, 1.f);
+    __syncthreads();
+    block_rfft<LOGB, NT>(X, last, tw);
+    for (int f = threadIdx.x; f <= N; f += NT) {
+      const float2 z = f < N ? X[pad_idx(f)] : *last;
+      if (j == 0) P[f] = z;
+      else if (j == 1) P[f] = cmul(P[f], z);
+      else Xm[f] = csub(Xm[f], cscale(cmul(P[f], z), lam));
+    }
+    __syncthreads();
+  }
 }
 
 // ------------------------------------------------------------------ sketched CP loss
@@ -403,6 +511,32 @@ static int launch_ivw(int log2b, const IvwArgs& a, cudaStream_t st) {
   }
 }
 
+template <int LOGB>
+static int launch_asym_deflate_t(float2* Xh, const int32_t* h, const uint8_t* g, int nmax,
+                                 const float* u, int n, const float* defl, float2* dspec, int B,
+                                 cudaStream_t st) {
+  constexpr size_t smem = asym_smem_bytes<LOGB>();
+  TSK_CUDA(tsk_smem_attr<asym_deflate_kernel<LOGB>>(smem));
+  asym_deflate_kernel<LOGB><<<B, asym_threads<LOGB>(), smem, st>>>(Xh, h, g, nmax, u, n, defl, dspec);
+  TSK_CHECK_LAUNCH();
+  return TSK_OK;
+}
+
+static int launch_asym_deflate(int log2b, float2* Xh, const int32_t* h, const uint8_t* g, int nmax,
+                               const float* u, int n, const float* defl, float2* dspec, int B,
+                               cudaStream_t st) {
+  switch (log2b) {
+    case 9: return launch_asym_deflate_t<9>(Xh, h, g, nmax, u, n, defl, dspec, B, st);
+    case 10: return launch_asym_deflate_t<10>(Xh, h, g, nmax, u, n, defl, dspec, B, st);
+    case 11: return launch_asym_deflate_t<11>(Xh, h, g, nmax, u, n, defl, dspec, B, st);
+    case 12: return launch_asym_deflate_t<12>(Xh, h, g, nmax, u, n, defl, dspec, B, st);
+    case 13: return launch_asym_deflate_t<13>(Xh, h, g, nmax, u, n, defl, dspec, B, st);
+    case 14: return launch_asym_deflate_t<14>(Xh, h, g, nmax, u, n, defl, dspec, B, st);
+    case 15: return launch_asym_deflate_t<15>(Xh, h, g, nmax, u, n, defl, dspec, B, st);
+    default: return TSK_EUNSUPPORTED;
+  }
+}
+
 static int launch_cp(int log2b, const CpArgs& a, bool with_grad, cudaStream_t st) {
   switch (log2b) {
     case 9: return launch_cp_t<9>(a, with_grad, st);
@@ -530,5 +664,85 @@ extern "C" int cp_als_solve(tsk_ctx* ctx, const float* M, const float* P, const 
   als_solve_kernel<<<1, 256, 0, ctx->stream>>>(M, P, Q, K, (int)n, (int)np, (int)nq, out, lam,
                                                ctx->status);
   TSK_CHECK_LAUNCH();
+  return TSK_OK;
+}
+
+extern "C" int robust_power_method_asym(tsk_ctx* ctx, const float* S, const int32_t* h,
+                                        const uint8_t* g, int B, int log2b, int64_t n, int k,
+                                        int L, int T, const float* U0, double* lambda,
+                                        float* Vout, int32_t* tau_star, float* lam_all_out,
+                                        float* U_iters) {
+  if (!ctx || !S || !h || !g) return TSK_EINVAL;
+  if (k < 0 || T < 1 || B < 1 || L < 1 || n < 1 || log2b < 1 || log2b > 24) return TSK_EINVAL;
+  if (log2b < 9 || log2b > 15 || B > kMaxB64 || n > 8192 || L > 65535) return TSK_EUNSUPPORTED;
+  if (k == 0) return TSK_OK;
+  if (!U0 || !lambda || !Vout) return TSK_EINVAL;
+  const size_t N = (size_t)1 << (log2b - 1);
+  auto carve = [&](WsCarve& wc, float2*& Xh, float2*& spec, float2*& dspec, float*& Vall,
+                   float*& Ua, float*& Ub, float*& lam, float*& defl, unsigned*& counters) {
+    Xh = wc.take<float2>((size_t)B * (N + 1));
+    spec = wc.take<float2>((size_t)L * B * (N + 1));
+    dspec = wc.take<float2>((size_t)B * (N + 1));
+    Vall = wc.take<float>((size_t)L * B * n);
+    Ua = wc.take<float>((size_t)L * n);
+    Ub = wc.take<float>((size_t)L * n);
+    lam = lam_all_out ? lam_all_out : wc.take<float>((size_t)k * L);
+    defl = wc.take<float>(1);
+    counters = wc.take<unsigned>(L);
+  };
+  float2 *Xh, *spec, *dspec;
+  float *Vall, *Ua, *Ub, *lam, *defl;
+  unsigned* counters;
+  WsCarve probe{nullptr, 0};
+  carve(probe, Xh, spec, dspec, Vall, Ua, Ub, lam, defl, counters);
+  int rc = tsk_ws_reserve(ctx, probe.off + 256);
+  if (rc != TSK_OK) return rc;
+  WsCarve wc{static_cast<char*>(ctx->ws), 0};
+  carve(wc, Xh, spec, dspec, Vall, Ua, Ub, lam, defl, counters);
+  cudaStream_t st = ctx->stream;
+  TSK_CUDA(cudaMemsetAsync(counters, 0, L * sizeof(unsigned), st));
+  if ((rc = launch_rfft(log2b, reinterpret_cast<const float2*>(S), Xh, B, st)) != TSK_OK) return rc;
+  IvwArgs a{};
+  a.Xh = Xh;
+  a.h = h;
+  a.g = g;
+  a.nmax = (int)n;
+  a.B = B;
+  a.K = L;
+  a.o = 0;
+  a.p = 1;
+  a.q = 2;
+  a.n_o = a.n_p = a.n_q = (int)n;
+  a.spec = spec;
+  a.Vall = Vall;
+  a.counters = counters;
+  for (int r = 0; r < k; ++r) {
+    normalize_rows_kernel<<<L, 256, 0, st>>>(U0 + (size_t)r * L * n, Ua, (int)n, ctx->status);
+    TSK_CHECK_LAUNCH();
+    const float* cur = Ua;
+    for (int t = 0; t < T; ++t) {
+      a.V = cur;
+      a.W = cur;
+      a.Vmed = Ub;
+      if ((rc = launch_ivw(log2b, a, st)) != TSK_OK) return rc;
+      float* next = U_iters ? U_iters + (((size_t)r * T + t) * L) * n : Ua;
+      normalize_rows_kernel<<<L, 256, 0, st>>>(Ub, next, (int)n, ctx->status);
+      TSK_CHECK_LAUNCH();
+      cur = next;
+    }
+    // selection with the per-sketch values of the final iterates
+    a.V = cur;
+    a.W = cur;
+    a.Vmed = Ub;
+    if ((rc = launch_ivw(log2b, a, st)) != TSK_OK) return rc;
+    float* lam_r = lam + (size_t)r * L;
+    asym_select_kernel<<<L, 256, 0, st>>>(cur, Vall, B, (int)n, lam_r);
+    TSK_CHECK_LAUNCH();
+    asym_pick_kernel<<<1, 256, 0, st>>>(lam_r, L, cur, (int)n, r, lambda, Vout, tau_star, defl);
+    TSK_CHECK_LAUNCH();
+    if ((rc = launch_asym_deflate(log2b, Xh, h, g, (int)n, Vout + (size_t)r * n, (int)n, defl,
+                                  dspec, B, st)) != TSK_OK)
+      return rc;
+  }
   return TSK_OK;
 }
