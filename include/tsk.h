@@ -102,7 +102,8 @@ int cs_hashes(tsk_ctx* ctx, uint64_t seed, int B, int log2b, int M, const int64_
  * in_dtype: TSK_F32 | TSK_F64 | TSK_I32.  acc_dtype: TSK_C64 (float accumulation, any input),
  *   TSK_C128 (double accumulation, F64 input) or TSK_CI64 (exact int64, I32 input).
  * S: [B][b] of acc_dtype.  accumulate = 0 overwrites S, 1 adds to it.
- * Limits: symmetric path log2b <= 14 (M = 1), n <= 8192. */
+ * Limits: symmetric path log2b <= 16 (M = 1; above 2^14 the buckets are built in 2 or 4
+ * ranges by separate blocks), asymmetric path log2b <= 15, n <= 8192. */
 int sketch_tensor(tsk_ctx* ctx, const void* T, int in_dtype, int M, const int64_t* dims_host,
                   const int32_t* h, const uint8_t* g, int B, int log2b,
                   void* S, int acc_dtype, int accumulate);
@@ -292,15 +293,20 @@ int lda_recover(tsk_ctx* ctx, const float* W, int64_t V, int k, double alpha0,
  * U_iters: optional [k][T][L][n] float, every iterate u_1..u_T of every round (diagnostics;
  *   lets a caller re-check each power update and selection independently).
  * A zero/non-finite norm in an update is reported by tsk_ctx_status() as TSK_ENONFINITE.
- * Limits: as contract_iuu, 1 <= L <= 4096, T >= 1, k >= 0. */
+ * Sketch lengths above 2^14 (log2b 15, 16) are split by frequency class f mod P over
+ * P = b / 2^14 blocks per (vector, sketch): block c scatters each nonzero of the count sketch
+ * with the twiddle w_b^(c p) into a length-b/P transform, and the read-off sums the P classes'
+ * inverses with w_b^(-c t) (an exact rewriting of the length-b DFT).
+ * Limits: log2b in [8, 16], 1 <= B <= 64, 1 <= n <= 8192, 1 <= L <= 4096, T >= 1, k >= 0. */
 int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* h, const uint8_t* g,
                         int B, int log2b, int64_t n, int k, int L, int T, const float* U0,
                         double* lambda, float* Vout, int32_t* tau_star, float* S_deflated,
                         float* lam_all, float* U_iters);
 
 /* Number of kernel launches robust_power_method makes for these sizes on ctx's device (one
- * batched DFT, then per round G groups x (T power steps + 1 selection) + 1 deflation, where G
- * is the number of helper-stream groups the L chains are split into).  -1 on bad sizes. */
+ * batched DFT, then per round G groups x (T power steps + 1 selection) + 1 deflation (+1 to
+ * assemble the time-domain update when log2b > 14), where G = min(L, 8) is the number of
+ * helper-stream groups the L chains are split into).  -1 on bad sizes. */
 int64_t robust_power_method_launches(tsk_ctx* ctx, int B, int log2b, int64_t n, int k, int L,
                                      int T);
 

@@ -8,11 +8,12 @@ namespace tsk {
 
 template <int LOGB, int MODE>
 static int launch_contract_t(const ContractArgs& a, cudaStream_t st) {
-  constexpr int NT = threads_for_logb(LOGB);
-  constexpr size_t smem = contract_smem_bytes<LOGB>();
-  TSK_CUDA(tsk_smem_attr<contract_kernel<LOGB, MODE>>(smem));
-  dim3 grid(a.B, a.L);
-  contract_kernel<LOGB, MODE><<<grid, NT, smem, st>>>(a);
+  constexpr int LOGP = LOGB > 14 ? LOGB - 14 : 0;
+  constexpr int NT = threads_for_logb(LOGB - LOGP);
+  constexpr size_t smem = contract_smem_bytes<LOGB - LOGP>();
+  TSK_CUDA(tsk_smem_attr<contract_kernel<LOGB, MODE, LOGP>>(smem));
+  dim3 grid(a.B << LOGP, a.L);
+  contract_kernel<LOGB, MODE, LOGP><<<grid, NT, smem, st>>>(a);
   TSK_CHECK_LAUNCH();
   return TSK_OK;
 }
@@ -32,18 +33,43 @@ int launch_contract(int log2b, int mode, const ContractArgs& a, cudaStream_t st)
     case 12: return launch_contract_mode<12>(mode, a, st);
     case 13: return launch_contract_mode<13>(mode, a, st);
     case 14: return launch_contract_mode<14>(mode, a, st);
+    case 15: return launch_contract_mode<15>(mode, a, st);
+    case 16: return launch_contract_mode<16>(mode, a, st);
     default: return TSK_EUNSUPPORTED;
   }
 }
 
 template <int LOGB>
 static int launch_deflate_t(const DeflateArgs& a, int B, cudaStream_t st) {
-  constexpr int NT = threads_for_logb(LOGB);
-  constexpr size_t smem = (size_t)padded_len(1 << LOGB) * sizeof(float2);
-  TSK_CUDA(tsk_smem_attr<deflate_kernel<LOGB>>(smem));
-  deflate_kernel<LOGB><<<B, NT, smem, st>>>(a);
+  constexpr int LOGP = LOGB > 14 ? LOGB - 14 : 0;
+  constexpr int NT = threads_for_logb(LOGB - LOGP);
+  constexpr size_t smem = (size_t)padded_len(1 << (LOGB - LOGP)) * sizeof(float2);
+  TSK_CUDA(tsk_smem_attr<deflate_kernel<LOGB, LOGP>>(smem));
+  deflate_kernel<LOGB, LOGP><<<B << LOGP, NT, smem, st>>>(a);
+  TSK_CHECK_LAUNCH();
+  if constexpr (LOGP > 0) {
+    deflate_combine_kernel<LOGB, LOGP><<<dim3(16, B), 256, 0, st>>>(a.S, a.G);
+    TSK_CHECK_LAUNCH();
+  }
+  return TSK_OK;
+}
+
+template <int LOGB>
+static int launch_fft_split_t(const float2* S, float2* FS, int B, cudaStream_t st) {
+  constexpr int LOGP = LOGB - 14;
+  constexpr size_t smem = (size_t)padded_len(1 << 14) * sizeof(float2);
+  TSK_CUDA(tsk_smem_attr<fft_split_kernel<LOGB, LOGP>>(smem));
+  fft_split_kernel<LOGB, LOGP><<<B << LOGP, threads_for_logb(14), smem, st>>>(S, FS);
   TSK_CHECK_LAUNCH();
   return TSK_OK;
+}
+
+int launch_fft_split(int log2b, const float2* S, float2* FS, int B, cudaStream_t st) {
+  switch (log2b) {
+    case 15: return launch_fft_split_t<15>(S, FS, B, st);
+    case 16: return launch_fft_split_t<16>(S, FS, B, st);
+    default: return TSK_EUNSUPPORTED;
+  }
 }
 
 int launch_deflate(int log2b, const DeflateArgs& a, int B, cudaStream_t st) {
@@ -55,6 +81,8 @@ int launch_deflate(int log2b, const DeflateArgs& a, int B, cudaStream_t st) {
     case 12: return launch_deflate_t<12>(a, B, st);
     case 13: return launch_deflate_t<13>(a, B, st);
     case 14: return launch_deflate_t<14>(a, B, st);
+    case 15: return launch_deflate_t<15>(a, B, st);
+    case 16: return launch_deflate_t<16>(a, B, st);
     default: return TSK_EUNSUPPORTED;
   }
 }
@@ -149,10 +177,11 @@ static long long rpm_groups(int L) {
 extern "C" int64_t robust_power_method_launches(tsk_ctx* ctx, int B, int log2b, int64_t n, int k,
                                                 int L, int T) {
   (void)n;
-  if (!ctx || k < 0 || B < 1 || L < 1 || T < 1 || log2b < 8 || log2b > 14) return -1;
+  if (!ctx || k < 0 || B < 1 || L < 1 || T < 1 || log2b < 8 || log2b > 16) return -1;
   if (k == 0) return 0;
   const long long G = rpm_groups(L);
-  return 1 + (int64_t)k * (G * (T + 1) + 1);
+  const int split = log2b > 14 ? 1 : 0;   // deflation adds a combine launch
+  return 1 + (int64_t)k * (G * (T + 1) + 1 + split);
 }
 
 extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* h,
@@ -163,7 +192,7 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
   if (!ctx || !S || !h || !g) return TSK_EINVAL;
   if (k < 0 || T < 0 || B < 1 || L < 1 || n < 1) return TSK_EINVAL;
   if (log2b < 1 || log2b > 24) return TSK_EINVAL;
-  if (log2b < 8 || log2b > 14 || B > kMaxB || n > 8192 || L > 4096 || T < 1)
+  if (log2b < 8 || log2b > 16 || B > kMaxB || n > 8192 || L > 4096 || T < 1)
     return TSK_EUNSUPPORTED;
   const size_t b = (size_t)1 << log2b;
   if (k == 0) {
@@ -173,9 +202,13 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
     return TSK_OK;
   }
   if (!U0 || !lambda || !Vout) return TSK_EINVAL;
-  const size_t need = 2 * ws_round(B * b * sizeof(float2)) + ws_round((size_t)L * B * n * 4) +
-                      ws_round((size_t)L * B * 4) + ws_round(2 * (size_t)L * n * 4) +
-                      ws_round((size_t)k * L * 4) + ws_round((size_t)L * 4);
+  // sketch lengths above 2^14 are split over P blocks per (vector, sketch): per-sketch values
+  // and eigenvalues are kept as P shares, and deflation needs a [B][b] staging buffer
+  const int P = split_parts(log2b);
+  const size_t need = 2 * ws_round(B * b * sizeof(float2)) + ws_round((size_t)L * B * P * n * 4) +
+                      ws_round((size_t)L * B * P * 4) + ws_round(2 * (size_t)L * n * 4) +
+                      ws_round((size_t)k * L * 4) + ws_round((size_t)L * 4) +
+                      (P > 1 ? ws_round(B * b * sizeof(float2)) : 0);
   int rc = tsk_ws_reserve(ctx, need);
   if (rc != TSK_OK) return rc;
   const long long G = rpm_groups(L);
@@ -183,15 +216,20 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
   WsCarve wc{static_cast<char*>(ctx->ws), 0};
   float2* Sw = wc.take<float2>(B * b);
   float2* FSw = wc.take<float2>(B * b);
-  float* Vall = wc.take<float>((size_t)L * B * n);
-  float* lam_all = wc.take<float>((size_t)L * B);
+  float* Vall = wc.take<float>((size_t)L * B * P * n);
+  float* lam_all = wc.take<float>((size_t)L * B * P);
   float* Ubuf = wc.take<float>(2 * (size_t)L * n);
   float* lam_med = lam_all_out ? lam_all_out : wc.take<float>((size_t)k * L);
   unsigned* counters = wc.take<unsigned>(L);
+  float2* Gdefl = P > 1 ? wc.take<float2>(B * b) : nullptr;
   cudaStream_t st = ctx->stream;
   TSK_CUDA(cudaMemsetAsync(counters, 0, L * sizeof(unsigned), st));
   TSK_CUDA(cudaMemcpyAsync(Sw, S, B * b * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-  if ((rc = launch_fft_batched(log2b, Sw, FSw, B, 0, st)) != TSK_OK) return rc;
+  if (P == 1) {
+    if ((rc = launch_fft_batched(log2b, Sw, FSw, B, 0, st)) != TSK_OK) return rc;
+  } else {
+    if ((rc = launch_fft_split(log2b, Sw, FSw, B, st)) != TSK_OK) return rc;
+  }
 
   ContractArgs a{};
   a.FS = FSw;
@@ -211,6 +249,7 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
   d.lambda_out = lambda;
   d.Vout = Vout;
   d.tau_out = tau_star;
+  d.G = Gdefl;
   for (int r = 0; r < k; ++r) {
     TSK_CUDA(cudaEventRecord(ctx->ev_fork, st));
     for (int s = 0; s < G; ++s) {
@@ -219,8 +258,8 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
       cudaStream_t gs = ctx->aux[s];
       TSK_CUDA(cudaStreamWaitEvent(gs, ctx->ev_fork, 0));
       a.L = Ls;
-      a.Vall = Vall + (size_t)tau0 * B * n;
-      a.lam_all = lam_all + (size_t)tau0 * B;
+      a.Vall = Vall + (size_t)tau0 * B * P * n;
+      a.lam_all = lam_all + (size_t)tau0 * B * P;
       a.counters = counters + tau0;
       const float* cur = U0 + ((size_t)r * L + tau0) * n;
       for (int t = 0; t < T; ++t) {

@@ -58,14 +58,25 @@ constexpr size_t contract_smem_bytes() {
 
 // One (vector, sketch) contraction.  MODE_IUU writes v^(m) to vout[0..n); both modes return
 // lambda^(m) = T^(m)(u,u,u) in every thread.  Must be called by all NT threads of the block.
-template <int LOGB, int MODE, int NT = threads_for_logb(LOGB)>
+//
+// Sketch lengths beyond one block (LOGP > 0, P = 2^LOGP): the block handles the residue class
+// `part` of the frequencies, f = P f' + part, with transforms of length M = b / P.  Splitting
+// the DFT by f mod P, X[P f' + c] = DFT_M(a_c)[f'] with a_c[p mod M] += x_p w_b^(c p), so each
+// count-sketch nonzero is scattered with one twiddle; on the way back the read-off output
+// g[t] = (1/b) sum_c w_b^(-c t) G_c[t mod M] is a sum over the P blocks, so each block writes its
+// share of v^(m) (the S[3 h_i] term goes with part 0) and the last block adds the P shares.
+template <int LOGB, int MODE, int NT = threads_for_logb(LOGB), int LOGP = 0>
 __device__ __forceinline__ float contract_one(float2* A, float2* Eb, float* red, const float2* tw,
                                               const float2* FSm, const float2* Sm,
                                               const int32_t* hm, const uint8_t* gm,
                                               const float* u, int n, bool normalize, int* status,
-                                              float* vout) {
+                                              float* vout, int part = 0) {
   constexpr int b = 1 << LOGB;
   constexpr int hb = b / 2;
+  constexpr int LOGM = LOGB - LOGP;
+  constexpr int M = 1 << LOGM;
+  constexpr int hM = M / 2;
+  constexpr int P = 1 << LOGP;
   constexpr float inv_b = 1.f / (float)b;
   const int tid = threadIdx.x;
 
@@ -86,60 +97,81 @@ __device__ __forceinline__ float contract_one(float2* A, float2* Eb, float* red,
   }
 
   // 1. zero both buffers, then scatter the count sketches of u.
-  for (int i = tid; i < padded_len(b); i += NT) A[i] = make_float2(0.f, 0.f);
-  for (int i = tid; i < padded_len(hb); i += NT) Eb[i] = make_float2(0.f, 0.f);
+  for (int i = tid; i < padded_len(M); i += NT) A[i] = make_float2(0.f, 0.f);
+  for (int i = tid; i < padded_len(hM); i += NT) Eb[i] = make_float2(0.f, 0.f);
   __syncthreads();
   for (int i = tid; i < n; i += NT) {
     const float x = __ldcg(u + i) * uscale;
     const int hi = hm[i] & (b - 1);
     const int gi = gm[i] & 3;
-    float* slot = reinterpret_cast<float*>(&A[pad_idx(hi)]);
-    atomicAdd(slot + (gi & 1), (gi & 2) ? -x : x);
-    atomicAdd(&Eb[pad_idx(hi & (hb - 1))].x, (gi & 1) ? -x * x : x * x);
+    if constexpr (LOGP == 0) {
+      float* slot = reinterpret_cast<float*>(&A[pad_idx(hi)]);
+      atomicAdd(slot + (gi & 1), (gi & 2) ? -x : x);
+      atomicAdd(&Eb[pad_idx(hi & (hb - 1))].x, (gi & 1) ? -x * x : x * x);
+    } else {
+      const float2 v = cmul(cmul_ipow(make_float2(x, 0.f), gi), unit_root_wide(tw, (part * hi) & (b - 1), b, -1));
+      float* slot = reinterpret_cast<float*>(&A[pad_idx(hi & (M - 1))]);
+      atomicAdd(slot, v.x);
+      atomicAdd(slot + 1, v.y);
+      const int h2 = hi & (hb - 1);
+      const float e = (gi & 1) ? -x * x : x * x;
+      const float2 w2 = unit_root(tw, (part * h2) & (hb - 1), hb, -1);
+      float* es = reinterpret_cast<float*>(&Eb[pad_idx(h2 & (hM - 1))]);
+      atomicAdd(es, e * w2.x);
+      atomicAdd(es + 1, e * w2.y);
+    }
   }
   __syncthreads();
 
   // 2. forward DFTs (the two transforms' passes interleaved).
-  block_fft_pair<LOGB, LOGB - 1, NT, -1>(A, Eb, tw);
+  block_fft_pair<LOGM, LOGM - 1, NT, -1>(A, Eb, tw);
 
   float lam = 0.f;
   if constexpr (MODE == MODE_IUU) {
     // 3. spectral products (each f < b/2 owns positions f and f + b/2 of A and f of Eb).
-    for (int f = tid; f < hb; f += NT) {
+    for (int f = tid; f < hM; f += NT) {
       const float2 cu0 = cconj(A[pad_idx(f)]);
-      const float2 cu1 = cconj(A[pad_idx(f + hb)]);
+      const float2 cu1 = cconj(A[pad_idx(f + hM)]);
       const float2 cv = cconj(Eb[pad_idx(f)]);
-      const float2 F0 = __ldcg(FSm + f);
-      const float2 F1 = __ldcg(FSm + f + hb);
+      const float2 F0 = __ldcg(FSm + P * f + part);
+      const float2 F1 = __ldcg(FSm + P * (f + hM) + part);
       A[pad_idx(f)] = cmul(F0, cadd(cmul(cu0, cu0), cv));
-      A[pad_idx(f + hb)] = cmul(F1, cadd(cmul(cu1, cu1), cv));
+      A[pad_idx(f + hM)] = cmul(F1, cadd(cmul(cu1, cu1), cv));
       Eb[pad_idx(f)] = cadd(cmul(F0, cu0), cmul(F1, cu1));
     }
     __syncthreads();
     // 4. inverse DFTs and hashed read-off.
-    block_fft_pair<LOGB, LOGB - 1, NT, +1>(A, Eb, tw);
+    block_fft_pair<LOGM, LOGM - 1, NT, +1>(A, Eb, tw);
     for (int i = tid; i < n; i += NT) {
       const float x = __ldcg(u + i) * uscale;
       const int hi = hm[i] & (b - 1);
       const int gi = gm[i] & 3;
-      const float2 g12 = A[pad_idx(hi)];
-      const float2 g0 = Eb[pad_idx(hi & (hb - 1))];
-      const float2 s3 = __ldcg(Sm + ((3 * hi) & (b - 1)));
-      const float v = (re_ipow(g12, -gi) * (1.f / 6.f) + re_ipow(g0, -2 * gi) * x * (1.f / 3.f)) * inv_b +
-                      re_ipow(s3, -3 * gi) * x * x * (1.f / 3.f);
+      float2 g12 = A[pad_idx(hi & (M - 1))];
+      float2 g0 = Eb[pad_idx(hi & (hM - 1))];
+      if constexpr (LOGP > 0) {
+        g12 = cmul(g12, unit_root_wide(tw, (part * hi) & (b - 1), b, +1));
+        const int h2 = hi & (hb - 1);
+        g0 = cmul(g0, unit_root(tw, (part * h2) & (hb - 1), hb, +1));
+      }
+      float v = (re_ipow(g12, -gi) * (1.f / 6.f) + re_ipow(g0, -2 * gi) * x * (1.f / 3.f)) * inv_b;
+      if (LOGP == 0 || part == 0) {
+        const float2 s3 = __ldcg(Sm + ((3 * hi) & (b - 1)));
+        v += re_ipow(s3, -3 * gi) * x * x * (1.f / 3.f);
+      }
       vout[i] = v;
       lam += x * v;
     }
   } else {
-    for (int f = tid; f < b; f += NT) {
+    for (int f = tid; f < M; f += NT) {
       const float2 U = A[pad_idx(f)];
-      const float2 V = Eb[pad_idx(f & (hb - 1))];
+      const float2 V = Eb[pad_idx(f & (hM - 1))];
       const float2 U2 = cmul(U, U);
       const float2 Y = cadd(cscale(cmul(U2, U), 1.f / 6.f), cscale(cmul(V, U), 0.5f));
-      const float2 F = __ldcg(FSm + f);
+      const float2 F = __ldcg(FSm + P * f + part);
       lam += F.x * Y.x + F.y * Y.y;     // Re(F conj(Y))
     }
     lam *= inv_b;
+    if (LOGP == 0 || part == 0)
     for (int i = tid; i < n; i += NT) {
       const float x = __ldcg(u + i) * uscale;
       const int hi = hm[i] & (b - 1);
@@ -171,17 +203,24 @@ __device__ __forceinline__ bool arrive_is_last(unsigned* counter, unsigned group
 // (its FFT buffers): each taking part thread sorts its B values in a column of it (entry c at
 // scratch[c * P + t], P threads taking part), not in a per-thread local-memory array, whose
 // traffic would go to L2 when shared memory leaves little L1.  Ends synchronised.
+//
+// With parts > 1 (sketch lengths split over several blocks), Vt is [B][parts][n] and each
+// sketch's value is the sum of its parts.
 template <int NT>
 __device__ __forceinline__ void median_vector(const float* Vt, int B, int n, float* dst,
                                               float* unext, float* red, int* status,
-                                              float* scratch, int scratch_floats) {
+                                              float* scratch, int scratch_floats, int parts = 1) {
   const int P = min(NT, scratch_floats / B);
   const int t = threadIdx.x;
   float ss = 0.f;
   if (t < P) {
     float* x = scratch + t;
     for (int i = t; i < n; i += P) {
-      for (int c = 0; c < B; ++c) x[c * P] = __ldcg(Vt + (size_t)c * n + i);
+      for (int c = 0; c < B; ++c) {
+        float v = __ldcg(Vt + (size_t)c * parts * n + i);
+        for (int q = 1; q < parts; ++q) v += __ldcg(Vt + ((size_t)c * parts + q) * n + i);
+        x[c * P] = v;
+      }
       const float med = small_median_strided(x, B, P);
       dst[i] = med;
       ss += med * med;
@@ -201,9 +240,13 @@ __device__ __forceinline__ void median_vector(const float* Vt, int B, int n, flo
   __syncthreads();
 }
 
-__device__ __forceinline__ float median_of(const float* x, int B) {
+__device__ __forceinline__ float median_of(const float* x, int B, int parts = 1) {
   float vals[kMaxB];
-  for (int c = 0; c < B; ++c) vals[c] = __ldcg(x + c);
+  for (int c = 0; c < B; ++c) {
+    float v = __ldcg(x + (size_t)c * parts);
+    for (int q = 1; q < parts; ++q) v += __ldcg(x + (size_t)c * parts + q);
+    vals[c] = v;
+  }
   return small_median(vals, B);
 }
 
@@ -238,6 +281,95 @@ __device__ __forceinline__ void deflate_one(float2* A, const float2* tw, float2*
   __syncthreads();
 }
 
+// Deflation of one frequency class of one sketch when the sketch length is split over P = 2^LOGP
+// blocks (see contract_one): U_c = DFT_M of the class's scattered count sketch, D_c = lambda^ U_c^3,
+// FS[P f' + part] -= D_c[f'], and the unnormalised inverse G_c = IDFT_M(D_c) is written to Gm; the
+// time-domain update S[t] -= (1/b) sum_c w_b^(-c t) G_c[t mod M] needs every class and is applied
+// by deflate_combine_kernel afterwards.
+template <int LOGB, int LOGP, int NT>
+__device__ __forceinline__ void deflate_part(float2* A, const float2* tw, float2* FSm, float2* Gm,
+                                             const int32_t* hm, const uint8_t* gm, const float* u,
+                                             int n, float lam, int part) {
+  constexpr int b = 1 << LOGB;
+  constexpr int LOGM = LOGB - LOGP;
+  constexpr int M = 1 << LOGM;
+  constexpr int P = 1 << LOGP;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < padded_len(M); i += NT) A[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int i = tid; i < n; i += NT) {
+    const int hi = hm[i] & (b - 1);
+    const float2 v = cmul(cmul_ipow(make_float2(__ldcg(u + i), 0.f), gm[i] & 3),
+                          unit_root_wide(tw, (part * hi) & (b - 1), b, -1));
+    float* slot = reinterpret_cast<float*>(&A[pad_idx(hi & (M - 1))]);
+    atomicAdd(slot, v.x);
+    atomicAdd(slot + 1, v.y);
+  }
+  __syncthreads();
+  block_fft<LOGM, NT, -1>(A, tw);
+  for (int f = tid; f < M; f += NT) {
+    const float2 U = A[pad_idx(f)];
+    const float2 D = cscale(cmul(cmul(U, U), U), lam);
+    FSm[P * f + part] = csub(__ldcg(FSm + P * f + part), D);
+    A[pad_idx(f)] = D;
+  }
+  __syncthreads();
+  block_fft<LOGM, NT, +1>(A, tw);
+  for (int t = tid; t < M; t += NT) Gm[t] = A[pad_idx(t)];
+  __syncthreads();
+}
+
+// S[m][t] -= (1/b) sum_c w_b^(-c t) G[m][c][t mod M] for the P frequency classes c (the inverse
+// DFT of the deflation term, assembled from the classes' length-M inverses).  Grid (chunks, B).
+template <int LOGB, int LOGP>
+__global__ void __launch_bounds__(256) deflate_combine_kernel(float2* S, const float2* G) {
+  constexpr int b = 1 << LOGB;
+  constexpr int M = 1 << (LOGB - LOGP);
+  constexpr int P = 1 << LOGP;
+  constexpr float inv_b = 1.f / (float)b;
+  __shared__ float2 tw[kTwEntries];
+  fill_twiddles(tw, 256);
+  const int m = blockIdx.y;
+  const float2* Gm = G + (size_t)m * P * M;
+  float2* Sm = S + (size_t)m * b;
+  for (int t = blockIdx.x * 256 + threadIdx.x; t < b; t += gridDim.x * 256) {
+    float2 acc = __ldcg(Gm + (t & (M - 1)));
+    for (int c = 1; c < P; ++c)
+      acc = cadd(acc, cmul(__ldcg(Gm + (size_t)c * M + (t & (M - 1))),
+                           unit_root_wide(tw, (c * t) & (b - 1), b, +1)));
+    Sm[t] = csub(__ldcg(Sm + t), cscale(acc, inv_b));
+  }
+}
+
+// FS = DFT_b of the sketches S when b is split over P blocks: block (m, c) forms
+// a_c[j] = sum_q S[m][j + q M] w_b^(c (j + q M)), j < M, and FS[m][P f' + c] = DFT_M(a_c)[f'].
+template <int LOGB, int LOGP>
+__global__ void __launch_bounds__(threads_for_logb(LOGB - LOGP), 1) fft_split_kernel(const float2* S,
+                                                                                    float2* FS) {
+  constexpr int LOGM = LOGB - LOGP;
+  constexpr int NT = threads_for_logb(LOGM);
+  constexpr int b = 1 << LOGB;
+  constexpr int M = 1 << LOGM;
+  constexpr int P = 1 << LOGP;
+  extern __shared__ float2 smem[];
+  __shared__ float2 tw[kTwEntries];
+  fill_twiddles(tw, NT);
+  const int m = blockIdx.x >> LOGP, c = blockIdx.x & (P - 1);
+  const float2* Sm = S + (size_t)m * b;
+  for (int j = threadIdx.x; j < M; j += NT) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int q = 0; q < P; ++q) {
+      const int t = j + q * M;
+      acc = cadd(acc, cmul(__ldcg(Sm + t), unit_root_wide(tw, (c * t) & (b - 1), b, -1)));
+    }
+    smem[pad_idx(j)] = acc;
+  }
+  __syncthreads();
+  block_fft<LOGM, NT, -1>(smem, tw);
+  float2* FSm = FS + (size_t)m * b;
+  for (int f = threadIdx.x; f < M; f += NT) FSm[P * f + c] = smem[pad_idx(f)];
+}
+
 // First index of the maximum of x[0..L) (the selection tau* of Alg. 1).
 __device__ __forceinline__ int first_argmax(const float* x, int L) {
   int best = 0;
@@ -254,36 +386,43 @@ __device__ __forceinline__ int first_argmax(const float* x, int L) {
 
 // ------------------------------------------------------------------ single-step kernels
 
-template <int LOGB, int MODE>
-__global__ void __launch_bounds__(threads_for_logb(LOGB),
-                                  contract_min_blocks(LOGB, threads_for_logb(LOGB)))
+// Grid (B P, L): block x handles sketch x / P and frequency class x mod P (P = 2^LOGP; Vall and
+// lam_all then hold [L][B][P] shares); the last of the B P blocks of a vector takes the medians.
+template <int LOGB, int MODE, int LOGP = 0>
+__global__ void __launch_bounds__(threads_for_logb(LOGB - LOGP),
+                                  contract_min_blocks(LOGB - LOGP, threads_for_logb(LOGB - LOGP)))
     contract_kernel(ContractArgs a) {
-  constexpr int NT = threads_for_logb(LOGB);
+  constexpr int LOGM = LOGB - LOGP;
+  constexpr int NT = threads_for_logb(LOGM);
   constexpr int b = 1 << LOGB;
+  constexpr int M = 1 << LOGM;
+  constexpr int P = 1 << LOGP;
   extern __shared__ float2 smem[];
   float2* A = smem;
-  float2* Eb = smem + padded_len(b);
-  float* red = reinterpret_cast<float*>(Eb + padded_len(b / 2));
+  float2* Eb = smem + padded_len(M);
+  float* red = reinterpret_cast<float*>(Eb + padded_len(M / 2));
   __shared__ int s_last;
   __shared__ float2 tw[kTwEntries];
   fill_twiddles(tw, NT);
-  const int m = blockIdx.x, tau = blockIdx.y, n = a.n, B = a.B;
-  const float lam = contract_one<LOGB, MODE>(
+  const int m = blockIdx.x >> LOGP, part = blockIdx.x & (P - 1);
+  const int tau = blockIdx.y, n = a.n, B = a.B;
+  const size_t share = ((size_t)tau * B + m) * P + part;
+  const float lam = contract_one<LOGB, MODE, NT, LOGP>(
       A, Eb, red, tw, a.FS + (size_t)m * b, a.S + (size_t)m * b, a.h + (size_t)m * n,
       a.g + (size_t)m * n, a.U + (size_t)tau * n, n, a.normalize_input != 0, a.status,
-      MODE == MODE_IUU ? a.Vall + ((size_t)tau * B + m) * n : nullptr);
-  if (threadIdx.x == 0) a.lam_all[(size_t)tau * B + m] = lam;
-  if (!arrive_is_last(&a.counters[tau], (unsigned)B, &s_last)) return;
+      MODE == MODE_IUU ? a.Vall + share * n : nullptr, part);
+  if (threadIdx.x == 0) a.lam_all[share] = lam;
+  if (!arrive_is_last(&a.counters[tau], (unsigned)(B * P), &s_last)) return;
   if (threadIdx.x == 0) {
-    if (a.lam_med) a.lam_med[tau] = median_of(a.lam_all + (size_t)tau * B, B);
+    if (a.lam_med) a.lam_med[tau] = median_of(a.lam_all + (size_t)tau * B * P, B, P);
     a.counters[tau] = 0u;
   }
   if constexpr (MODE == MODE_IUU) {
     if (a.Vmed == nullptr && a.Unext == nullptr) return;
     float* dst = a.Vmed ? a.Vmed + (size_t)tau * n : a.Unext + (size_t)tau * n;
-    median_vector<NT>(a.Vall + (size_t)tau * B * n, B, n, dst,
+    median_vector<NT>(a.Vall + (size_t)tau * B * P * n, B, n, dst,
                       a.Unext ? a.Unext + (size_t)tau * n : nullptr, red, a.status,
-                      reinterpret_cast<float*>(A), 2 * (padded_len(b) + padded_len(b / 2)));
+                      reinterpret_cast<float*>(A), 2 * (padded_len(M) + padded_len(M / 2)), P);
   }
 }
 
@@ -303,35 +442,47 @@ struct DeflateArgs {
   double* lambda_out;       // [k]
   float* Vout;              // [k][n]
   int32_t* tau_out;         // [k] or NULL
+  float2* G;                // [B][P][b/P] workspace when the sketch length is split (P > 1)
 };
 
-template <int LOGB>
-__global__ void __launch_bounds__(threads_for_logb(LOGB), 1) deflate_kernel(DeflateArgs a) {
-  constexpr int NT = threads_for_logb(LOGB);
+template <int LOGB, int LOGP = 0>
+__global__ void __launch_bounds__(threads_for_logb(LOGB - LOGP), 1) deflate_kernel(DeflateArgs a) {
+  constexpr int LOGM = LOGB - LOGP;
+  constexpr int NT = threads_for_logb(LOGM);
   constexpr int b = 1 << LOGB;
+  constexpr int P = 1 << LOGP;
   extern __shared__ float2 smem[];
   __shared__ int s_best;
   __shared__ float2 tw[kTwEntries];
   fill_twiddles(tw, NT);
-  const int m = blockIdx.x, n = a.n;
+  const int m = blockIdx.x >> LOGP, part = blockIdx.x & (P - 1), n = a.n;
   if (threadIdx.x == 0) s_best = first_argmax(a.lam_med, a.L);
   __syncthreads();
   const int best = s_best;
   const float lam = a.lam_med[best];
   const float* u = a.Ufinal + (size_t)best * n;
-  if (m == 0) {
+  if (blockIdx.x == 0) {
     if (threadIdx.x == 0) {
       a.lambda_out[a.round] = (double)lam;
       if (a.tau_out) a.tau_out[a.round] = best;
     }
     for (int i = threadIdx.x; i < n; i += NT) a.Vout[(size_t)a.round * n + i] = u[i];
   }
-  deflate_one<LOGB>(smem, tw, a.FS + (size_t)m * b, a.S + (size_t)m * b, a.h + (size_t)m * n,
-                    a.g + (size_t)m * n, u, n, lam);
+  if constexpr (LOGP == 0) {
+    deflate_one<LOGB>(smem, tw, a.FS + (size_t)m * b, a.S + (size_t)m * b, a.h + (size_t)m * n,
+                      a.g + (size_t)m * n, u, n, lam);
+  } else {
+    deflate_part<LOGB, LOGP, NT>(smem, tw, a.FS + (size_t)m * b,
+                                 a.G + ((size_t)m * P + part) * (b / P), a.h + (size_t)m * n,
+                                 a.g + (size_t)m * n, u, n, lam, part);
+  }
 }
 
 // Host launchers (defined in contract.cu).
 int launch_contract(int log2b, int mode, const ContractArgs& args, cudaStream_t st);
 int launch_deflate(int log2b, const DeflateArgs& args, int B, cudaStream_t st);
+int launch_fft_split(int log2b, const float2* S, float2* FS, int B, cudaStream_t st);
+// Blocks per (vector, sketch) at sketch length 2^log2b: 1 up to 2^14, then b / 2^14.
+constexpr int split_parts(int log2b) { return log2b > 14 ? 1 << (log2b - 14) : 1; }
 
 }  // namespace tsk

@@ -99,7 +99,7 @@ __device__ __forceinline__ void fill_twiddles(float2* tw, int nt) {
   __syncthreads();
 }
 
-// exp(DIR * 2 pi i * k / span), span a power of two <= 2^15.
+// exp(DIR * 2 pi i * k / span), span a power of two <= 2^15, 0 <= k < span.
 TSK_HD float2 unit_root(const float2* tw, int k, int span, int dir) {
 #ifdef __CUDA_ARCH__
   const int m = k * ((1 << kTwLog) / span);
@@ -110,6 +110,18 @@ TSK_HD float2 unit_root(const float2* tw, int k, int span, int dir) {
   const double a = 2.0 * 3.14159265358979323846 * (double)k / (double)span;
   return make_float2((float)cos(a), (float)(dir > 0 ? sin(a) : -sin(a)));
 #endif
+}
+
+// exp(DIR * 2 pi i * k / span) for spans up to 2^16: a 2^16 root with an odd exponent is the
+// table's 2^15 root times exp(DIR * 2 pi i / 2^16) (used by the sketch-length splits only).
+__device__ __forceinline__ float2 unit_root_wide(const float2* tw, int k, int span, int dir) {
+  if (span <= (1 << kTwLog)) return unit_root(tw, k, span, dir);
+  const float2 w = unit_root(tw, k >> 1, span >> 1, dir);
+  if (!(k & 1)) return w;
+  // cos and sin of 2 pi / 2^16 (decimal expansions of the mathematical constants)
+  const float2 r = make_float2(0.99999999540410766f, dir > 0 ? 9.5873799095977345e-5f
+                                                             : -9.5873799095977345e-5f);
+  return cmul(w, r);
 }
 
 // v[r] *= w^r, w = exp(DIR 2 pi i k / span), r = 1..R-1.  w^2, w^4, w^8 are formed by

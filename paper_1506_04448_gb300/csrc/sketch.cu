@@ -43,22 +43,29 @@ struct SymSketchArgs {
   long long W;        // wedge size n(n+1)(n+2)/6
   int nslab;
   void* S;            // [B][b][2] accumulator type
+  int log2r;          // the buckets are split into 2^log2r ranges, one block per range
 };
 
-template <typename TIn, typename Acc, int PARTS>
+template <typename TIn, typename Acc, int PARTS, bool RANGES = false>
 __global__ void __launch_bounds__(1024, 1) sketch_sym_kernel(SymSketchArgs a) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ int s_i0, s_j0, s_i1, s_j1;
   const int b = 1 << a.log2b;
   const int n = a.n;
   const int mask = b - 1;
-  const int hist_len = (PARTS == 1 ? 2 : 1) * b;
+  // this block's bucket range [rr br, (rr + 1) br): long sketches do not fit one block's shared
+  // memory, so they are built by 2^log2r blocks that each keep the entries of their range
+  const int R = RANGES ? 1 << a.log2r : 1;
+  const int br = RANGES ? b >> a.log2r : b;
+  const int hist_len = (PARTS == 1 ? 2 : 1) * br;
   Acc* hist = reinterpret_cast<Acc*>(sm_raw);
   // packed hash word q_k = 16 h_k + g_k: in q_i + q_j + q_k, bits 4.. carry h_i + h_j + h_k and
   // bits 0..3 carry g_i + g_j + g_k (at most 9), so one add gives bucket and sign exponent
   uint32_t* qs = reinterpret_cast<uint32_t*>(sm_raw + (size_t)hist_len * sizeof(Acc));
-  const int m = blockIdx.x / PARTS;
-  const int part = blockIdx.x % PARTS;
+  const int m = blockIdx.x / (PARTS * R);
+  const int part = (blockIdx.x / R) % PARTS;
+  const int rr = blockIdx.x % R;
+  const int shift_r = a.log2b - a.log2r;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < hist_len; i += nt) hist[i] = (Acc)0;
   for (int i = tid; i < n; i += nt)
@@ -123,17 +130,19 @@ __global__ void __launch_bounds__(1024, 1) sketch_sym_kernel(SymSketchArgs a) {
         Acc v = (Acc)x[q] * (k == j ? kap_diag : kap_off);
         if (sq & 2) v = -v;
         const int t = (int)(sq >> 4) & mask;
+        if (RANGES && (t >> shift_r) != rr) continue;
+        const int tl = RANGES ? t & (br - 1) : t;
         if (PARTS == 1) {
-          acc_add<Acc>(&hist[2 * t + (int)(sq & 1)], v);
+          acc_add<Acc>(&hist[2 * tl + (int)(sq & 1)], v);
         } else if ((int)(sq & 1) == part) {
-          acc_add<Acc>(&hist[t], v);
+          acc_add<Acc>(&hist[tl], v);
         }
       }
     }
     advance(i, j, nw);
   }
   __syncthreads();
-  Acc* Sg = static_cast<Acc*>(a.S) + (size_t)m * 2 * b;
+  Acc* Sg = static_cast<Acc*>(a.S) + (size_t)m * 2 * b + (size_t)2 * rr * br;
   for (int idx = tid; idx < hist_len; idx += nt) {
     const Acc v = hist[idx];
     if (v != (Acc)0) acc_add<Acc>(&Sg[PARTS == 1 ? idx : 2 * idx + part], v);
@@ -213,23 +222,30 @@ template <typename TIn, typename Acc, int PARTS>
 static int launch_sym(const SymSketchArgs& a0, int B, tsk_ctx* ctx) {
   SymSketchArgs a = a0;
   const int b = 1 << a.log2b;
-  const size_t smem = (size_t)(PARTS == 1 ? 2 : 1) * b * sizeof(Acc) + (size_t)a.n * 4 + 16;
+  // fewest bucket ranges whose histogram fits the block's shared memory
+  a.log2r = 0;
+  size_t smem = 0;
+  for (;; ++a.log2r) {
+    smem = (size_t)(PARTS == 1 ? 2 : 1) * (b >> a.log2r) * sizeof(Acc) + (size_t)a.n * 4 + 16;
+    if (smem <= (size_t)ctx->max_smem_optin || a.log2r >= 4) break;
+  }
+  const int R = 1 << a.log2r;
   if (smem > (size_t)ctx->max_smem_optin) return TSK_EUNSUPPORTED;
-  TSK_CUDA(cudaFuncSetAttribute(sketch_sym_kernel<TIn, Acc, PARTS>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  auto kernel = a.log2r > 0 ? sketch_sym_kernel<TIn, Acc, PARTS, true>
+                            : sketch_sym_kernel<TIn, Acc, PARTS, false>;
+  TSK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  TSK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sketch_sym_kernel<TIn, Acc, PARTS>,
-                                                         1024, smem));
+  TSK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 1024, smem));
   if (per_sm < 1) per_sm = 1;
   // one wave of blocks over the SMs, but no more slabs than ~16k entries each
-  long long nslab = ((long long)ctx->num_sms * per_sm) / (B * PARTS);
+  long long nslab = ((long long)ctx->num_sms * per_sm) / (B * PARTS * R);
   if (nslab < 1) nslab = 1;
   const long long cap = (a.W + 16383) / 16384;
   if (nslab > cap) nslab = cap < 1 ? 1 : cap;
   if (nslab > 65535) nslab = 65535;
   a.nslab = (int)nslab;
-  dim3 grid(B * PARTS, (unsigned)nslab);
-  sketch_sym_kernel<TIn, Acc, PARTS><<<grid, 1024, smem, ctx->stream>>>(a);
+  dim3 grid(B * PARTS * R, (unsigned)nslab);
+  kernel<<<grid, 1024, smem, ctx->stream>>>(a);
   TSK_CHECK_LAUNCH();
   return TSK_OK;
 }
@@ -433,8 +449,8 @@ extern "C" int sketch_tensor(tsk_ctx* ctx, const void* T, int in_dtype, int M,
   if (M == 1) {
     const int n = (int)dims_host[0];
     if (n == 0) return TSK_OK;
-    if (log2b > 14) return TSK_EUNSUPPORTED;
-    SymSketchArgs a{T, n, h, g, log2b, (long long)n * (n + 1) * (n + 2) / 6, 1, S};
+    if (log2b > 16) return TSK_EUNSUPPORTED;
+    SymSketchArgs a{T, n, h, g, log2b, (long long)n * (n + 1) * (n + 2) / 6, 1, S, 0};
     if (acc_dtype == TSK_C64) {
       if (in_dtype == TSK_F32) return launch_sym<float, float, 1>(a, B, ctx);
       if (in_dtype == TSK_F64) return launch_sym<double, float, 1>(a, B, ctx);

@@ -46,7 +46,8 @@ def test_hashes_bit_exact(dev, seed, B, log2b, dims):
 
 
 # ------------------------------------------------------------------ sketch construction
-@pytest.mark.parametrize("n,log2b,B", [(1, 8, 1), (9, 8, 3), (30, 10, 2), (65, 12, 4)])
+@pytest.mark.parametrize("n,log2b,B", [(1, 8, 1), (9, 8, 3), (30, 10, 2), (65, 12, 4),
+                                       (30, 15, 2), (21, 16, 2)])   # bucket ranges split over blocks
 def test_symmetric_int_sketch_bit_exact(dev, n, log2b, B):
     b = 1 << log2b
     Ti = synth.random_symmetric_int(n, 100 + n)
@@ -59,7 +60,8 @@ def test_symmetric_int_sketch_bit_exact(dev, n, log2b, B):
         np.testing.assert_array_equal(S[m, :, 1], ref[1])
 
 
-@pytest.mark.parametrize("n,log2b,B", [(5, 8, 2), (37, 10, 3), (100, 14, 2)])
+@pytest.mark.parametrize("n,log2b,B", [(5, 8, 2), (37, 10, 3), (100, 14, 2), (40, 15, 2),
+                                       (40, 16, 3)])
 def test_symmetric_float_sketch(dev, n, log2b, B):
     b = 1 << log2b
     T = synth.random_symmetric(n, 200 + n)
@@ -234,7 +236,9 @@ def _run_rtpm(dev, n, k, L, T_it, B, log2b, seed, noise):
     (50, 5, 10, 20, 5, 10, 0.01),     # the small planted configuration
     (37, 3, 4, 6, 4, 9, 0.1),         # ragged n, even B
     (16, 2, 3, 5, 1, 8, 0.05),        # a single sketch (median of one)
-    (24, 2, 3, 4, 40, 10, 0.01)])     # B = 40 as in the paper's largest sketch count
+    (24, 2, 3, 4, 40, 10, 0.01),      # B = 40 as in the paper's largest sketch count
+    (20, 2, 3, 4, 3, 15, 0.02),       # b = 2^15: frequencies split over 2 blocks
+    (18, 2, 2, 3, 2, 16, 0.02)])      # b = 2^16: split over 4 blocks
 def test_rtpm_stepwise_parity(dev, n, k, L, T_it, B, log2b, noise):
     from rtpm_check import check_rtpm_stepwise
     res, Sg, ho, go, U0g, _, _ = _run_rtpm(dev, n, k, L, T_it, B, log2b, 1, noise)
