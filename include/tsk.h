@@ -344,8 +344,9 @@ int tsk_batch_create(tsk_ctx* ctx, const tsk_problem* problems, int P, int B, in
  * problem).  Allocates nothing and synchronises nothing, so it can be captured into one CUDA
  * graph and replayed; each run starts from the problems' S and U0 again. */
 int tsk_batch_run(tsk_ctx* ctx, tsk_batch* batch);
-int tsk_batch_destroy(tsk_batch* batch);
-/* Block size chosen for the group of sketch length 2^log2b (0 if the plan has no such group). */
+int tsk_batch_destroy(tsk_batch* batch);   /* TSK_EINVAL for NULL */
+/* Block size chosen for the group of sketch length 2^log2b (0 if the plan has no such group,
+ * TSK_EINVAL for a NULL plan). */
 int tsk_batch_block_size(const tsk_batch* batch, int log2b);
 /* create (without autotuning) + run + synchronise + destroy. */
 int robust_power_method_batched(tsk_ctx* ctx, const tsk_problem* problems, int P, int B, int L,

@@ -68,3 +68,30 @@ def test_binding_fails_loudly_when_library_missing(monkeypatch):
 
 def test_launch_count_query_rejects_a_null_context(lib):
     assert lib.robust_power_method_launches(None, 10, 14, 400, 20, 50, 30) == -1
+
+
+def test_every_compute_entry_rejects_a_null_context(lib):
+    """Each compute entry point of include/tsk.h returns TSK_EINVAL for a NULL context (or NULL
+    buffers) before anything reaches a device."""
+    from paper_1506_04448_gb300 import _lib
+    skip = {"tsk_ctx_create", "tsk_ctx_destroy", "tsk_ctx_set_stream", "tsk_ctx_status",
+            "tsk_strerror", "tsk_batch_destroy", "tsk_batch_block_size",
+            "robust_power_method_launches", "contract_iuu_static"}
+    checked = 0
+    for name, (_, argtypes) in _lib.SIGNATURES.items():
+        if name in skip:
+            continue
+        args = [0 if t in (ctypes.c_int, ctypes.c_int64, ctypes.c_uint64) else
+                (0.0 if t is ctypes.c_double else None) for t in argtypes]
+        assert getattr(lib, name)(*args) == -1, name
+        checked += 1
+    assert checked >= 20
+
+
+def test_static_contraction_rejects_null_buffers(lib):
+    assert lib.contract_iuu_static(None, None, None, None, 1, 10, None, 1, 1, None, None) == -1
+
+
+def test_batch_entry_points_reject_null_plans(lib):
+    assert lib.tsk_batch_destroy(None) == -1
+    assert lib.tsk_batch_block_size(None, 10) == -1
