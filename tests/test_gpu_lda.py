@@ -187,3 +187,24 @@ def test_spectral_lda_recovers_planted_topics():
         j = int(np.argmin(np.abs(mu - Phi[i]).sum(1)))
         assert np.abs(mu[j] - Phi[i]).sum() < 0.25, (i, np.abs(mu[j] - Phi[i]).sum())
         assert abs(al[j] - alpha) < 0.5 * alpha
+
+
+def test_whitened_m3_at_benchmark_dimensions():
+    """V = 50000 words and k = 100 topics as in the benchmarked corpus (13 blocks of 8 topics,
+    3640 wedge units, 104-wide padded rows), with 4000 documents so that the oracle's streamed
+    O(nnz k) contractions stay cheap; random whitening matrix (the dense M2 of V = 50000 is
+    beyond the oracle)."""
+    T = tsk()
+    V, k, D = 50000, 100, 4000
+    c = synth.lda_corpus(V, k, D, 31, alpha=0.1, beta=0.01, mean_len=200)
+    a0 = k * 0.1
+    W = (synth.gaussian_matrix(V, k, 32) / np.sqrt(V)).astype(np.float32)
+    M3 = T.lda_whitened_m3(*on_dev(c), V, torch.from_numpy(W).to(dev), a0).cpu().double().numpy()
+    T.check_status(dev)
+    assert np.array_equal(M3, M3.transpose(1, 0, 2)) and np.array_equal(M3, M3.transpose(0, 2, 1))
+    for s in range(3):
+        x = synth.rng(50 + s).standard_normal(k)
+        xxx, ixx = L.whitened_m3_contract(c, W.astype(np.float64), a0, x)
+        tol = 2e-5 * np.abs(M3).max() * np.abs(x).sum() ** 2
+        np.testing.assert_allclose(np.einsum("abc,b,c->a", M3, x, x), ixx, rtol=0, atol=tol)
+        assert abs(np.einsum("abc,a,b,c", M3, x, x, x) - xxx) <= tol * np.abs(x).sum()
