@@ -6,9 +6,14 @@
 
 namespace tsk {
 
-template <int LOGB, int MODE>
+// Valid (log2 b, log2 P) pairs: one block per (vector, sketch) up to b = 2^14, or the
+// frequencies split into P classes whose transforms have length b / P = 2^13 or 2^14.
+constexpr bool split_ok(int logb, int logp) {
+  return logp >= 0 && logb - logp >= 8 && logb - logp <= 14 && (logp == 0 || logb - logp >= 12);
+}
+
+template <int LOGB, int LOGP, int MODE>
 static int launch_contract_t(const ContractArgs& a, cudaStream_t st) {
-  constexpr int LOGP = LOGB > 14 ? LOGB - 14 : 0;
   constexpr int NT = threads_for_logb(LOGB - LOGP);
   constexpr size_t smem = contract_smem_bytes<LOGB - LOGP>();
   TSK_CUDA(tsk_smem_attr<contract_kernel<LOGB, MODE, LOGP>>(smem));
@@ -18,71 +23,110 @@ static int launch_contract_t(const ContractArgs& a, cudaStream_t st) {
   return TSK_OK;
 }
 
-template <int LOGB>
-static int launch_contract_mode(int mode, const ContractArgs& a, cudaStream_t st) {
-  return mode == MODE_IUU ? launch_contract_t<LOGB, MODE_IUU>(a, st)
-                          : launch_contract_t<LOGB, MODE_UUU>(a, st);
-}
-
-int launch_contract(int log2b, int mode, const ContractArgs& a, cudaStream_t st) {
-  switch (log2b) {
-    case 8: return launch_contract_mode<8>(mode, a, st);
-    case 9: return launch_contract_mode<9>(mode, a, st);
-    case 10: return launch_contract_mode<10>(mode, a, st);
-    case 11: return launch_contract_mode<11>(mode, a, st);
-    case 12: return launch_contract_mode<12>(mode, a, st);
-    case 13: return launch_contract_mode<13>(mode, a, st);
-    case 14: return launch_contract_mode<14>(mode, a, st);
-    case 15: return launch_contract_mode<15>(mode, a, st);
-    case 16: return launch_contract_mode<16>(mode, a, st);
-    default: return TSK_EUNSUPPORTED;
+template <int LOGB, int LOGP>
+static int launch_contract_p(int mode, const ContractArgs& a, cudaStream_t st) {
+  if constexpr (split_ok(LOGB, LOGP)) {
+    return mode == MODE_IUU ? launch_contract_t<LOGB, LOGP, MODE_IUU>(a, st)
+                            : launch_contract_t<LOGB, LOGP, MODE_UUU>(a, st);
+  } else {
+    return TSK_EUNSUPPORTED;
   }
 }
 
 template <int LOGB>
+static int launch_contract_b(int logp, int mode, const ContractArgs& a, cudaStream_t st) {
+  switch (logp) {
+    case 0: return launch_contract_p<LOGB, 0>(mode, a, st);
+    case 1: return launch_contract_p<LOGB, 1>(mode, a, st);
+    case 2: return launch_contract_p<LOGB, 2>(mode, a, st);
+    case 3: return launch_contract_p<LOGB, 3>(mode, a, st);
+    default: return TSK_EUNSUPPORTED;
+  }
+}
+
+int launch_contract(int log2b, int logp, int mode, const ContractArgs& a, cudaStream_t st) {
+  switch (log2b) {
+    case 8: return launch_contract_b<8>(logp, mode, a, st);
+    case 9: return launch_contract_b<9>(logp, mode, a, st);
+    case 10: return launch_contract_b<10>(logp, mode, a, st);
+    case 11: return launch_contract_b<11>(logp, mode, a, st);
+    case 12: return launch_contract_b<12>(logp, mode, a, st);
+    case 13: return launch_contract_b<13>(logp, mode, a, st);
+    case 14: return launch_contract_b<14>(logp, mode, a, st);
+    case 15: return launch_contract_b<15>(logp, mode, a, st);
+    case 16: return launch_contract_b<16>(logp, mode, a, st);
+    default: return TSK_EUNSUPPORTED;
+  }
+}
+
+template <int LOGB, int LOGP>
 static int launch_deflate_t(const DeflateArgs& a, int B, cudaStream_t st) {
-  constexpr int LOGP = LOGB > 14 ? LOGB - 14 : 0;
-  constexpr int NT = threads_for_logb(LOGB - LOGP);
-  constexpr size_t smem = (size_t)padded_len(1 << (LOGB - LOGP)) * sizeof(float2);
-  TSK_CUDA(tsk_smem_attr<deflate_kernel<LOGB, LOGP>>(smem));
-  deflate_kernel<LOGB, LOGP><<<B << LOGP, NT, smem, st>>>(a);
-  TSK_CHECK_LAUNCH();
-  if constexpr (LOGP > 0) {
-    deflate_combine_kernel<LOGB, LOGP><<<dim3(16, B), 256, 0, st>>>(a.S, a.G);
+  if constexpr (split_ok(LOGB, LOGP)) {
+    constexpr int NT = threads_for_logb(LOGB - LOGP);
+    constexpr size_t smem = (size_t)padded_len(1 << (LOGB - LOGP)) * sizeof(float2);
+    TSK_CUDA(tsk_smem_attr<deflate_kernel<LOGB, LOGP>>(smem));
+    deflate_kernel<LOGB, LOGP><<<B << LOGP, NT, smem, st>>>(a);
     TSK_CHECK_LAUNCH();
+    if constexpr (LOGP > 0) {
+      deflate_combine_kernel<LOGB, LOGP><<<dim3(16, B), 256, 0, st>>>(a.S, a.G);
+      TSK_CHECK_LAUNCH();
+    }
+    return TSK_OK;
+  } else {
+    return TSK_EUNSUPPORTED;
   }
-  return TSK_OK;
 }
 
 template <int LOGB>
-static int launch_fft_split_t(const float2* S, float2* FS, int B, cudaStream_t st) {
-  constexpr int LOGP = LOGB - 14;
-  constexpr size_t smem = (size_t)padded_len(1 << 14) * sizeof(float2);
-  TSK_CUDA(tsk_smem_attr<fft_split_kernel<LOGB, LOGP>>(smem));
-  fft_split_kernel<LOGB, LOGP><<<B << LOGP, threads_for_logb(14), smem, st>>>(S, FS);
-  TSK_CHECK_LAUNCH();
-  return TSK_OK;
-}
-
-int launch_fft_split(int log2b, const float2* S, float2* FS, int B, cudaStream_t st) {
-  switch (log2b) {
-    case 15: return launch_fft_split_t<15>(S, FS, B, st);
-    case 16: return launch_fft_split_t<16>(S, FS, B, st);
+static int launch_deflate_b(int logp, const DeflateArgs& a, int B, cudaStream_t st) {
+  switch (logp) {
+    case 0: return launch_deflate_t<LOGB, 0>(a, B, st);
+    case 1: return launch_deflate_t<LOGB, 1>(a, B, st);
+    case 2: return launch_deflate_t<LOGB, 2>(a, B, st);
+    case 3: return launch_deflate_t<LOGB, 3>(a, B, st);
     default: return TSK_EUNSUPPORTED;
   }
 }
 
-int launch_deflate(int log2b, const DeflateArgs& a, int B, cudaStream_t st) {
+int launch_deflate(int log2b, int logp, const DeflateArgs& a, int B, cudaStream_t st) {
   switch (log2b) {
-    case 8: return launch_deflate_t<8>(a, B, st);
-    case 9: return launch_deflate_t<9>(a, B, st);
-    case 10: return launch_deflate_t<10>(a, B, st);
-    case 11: return launch_deflate_t<11>(a, B, st);
-    case 12: return launch_deflate_t<12>(a, B, st);
-    case 13: return launch_deflate_t<13>(a, B, st);
-    case 14: return launch_deflate_t<14>(a, B, st);
-    case 15: return launch_deflate_t<15>(a, B, st);
-    case 16: return launch_deflate_t<16>(a, B, st);
+    case 8: return launch_deflate_b<8>(logp, a, B, st);
+    case 9: return launch_deflate_b<9>(logp, a, B, st);
+    case 10: return launch_deflate_b<10>(logp, a, B, st);
+    case 11: return launch_deflate_b<11>(logp, a, B, st);
+    case 12: return launch_deflate_b<12>(logp, a, B, st);
+    case 13: return launch_deflate_b<13>(logp, a, B, st);
+    case 14: return launch_deflate_b<14>(logp, a, B, st);
+    case 15: return launch_deflate_b<15>(logp, a, B, st);
+    case 16: return launch_deflate_b<16>(logp, a, B, st);
+    default: return TSK_EUNSUPPORTED;
+  }
+}
+
+template <int LOGB, int LOGP>
+static int launch_fft_split_t(const float2* S, float2* FS, int B, cudaStream_t st) {
+  if constexpr (LOGP > 0 && split_ok(LOGB, LOGP)) {
+    constexpr int LOGM = LOGB - LOGP;
+    constexpr size_t smem = (size_t)padded_len(1 << LOGM) * sizeof(float2);
+    TSK_CUDA(tsk_smem_attr<fft_split_kernel<LOGB, LOGP>>(smem));
+    fft_split_kernel<LOGB, LOGP><<<B << LOGP, threads_for_logb(LOGM), smem, st>>>(S, FS);
+    TSK_CHECK_LAUNCH();
+    return TSK_OK;
+  } else {
+    return TSK_EUNSUPPORTED;
+  }
+}
+
+int launch_fft_split(int log2b, int logp, const float2* S, float2* FS, int B, cudaStream_t st) {
+  switch (log2b * 4 + logp) {
+    case 13 * 4 + 1: return launch_fft_split_t<13, 1>(S, FS, B, st);
+    case 14 * 4 + 1: return launch_fft_split_t<14, 1>(S, FS, B, st);
+    case 14 * 4 + 2: return launch_fft_split_t<14, 2>(S, FS, B, st);
+    case 15 * 4 + 1: return launch_fft_split_t<15, 1>(S, FS, B, st);
+    case 15 * 4 + 2: return launch_fft_split_t<15, 2>(S, FS, B, st);
+    case 15 * 4 + 3: return launch_fft_split_t<15, 3>(S, FS, B, st);
+    case 16 * 4 + 2: return launch_fft_split_t<16, 2>(S, FS, B, st);
+    case 16 * 4 + 3: return launch_fft_split_t<16, 3>(S, FS, B, st);
     default: return TSK_EUNSUPPORTED;
   }
 }
@@ -131,7 +175,7 @@ extern "C" int contract_iuu(tsk_ctx* ctx, const float* FS, const float* S, const
   a.Unext = nullptr;
   a.lam_med = nullptr;
   a.status = ctx->status;
-  return launch_contract(log2b, MODE_IUU, a, ctx->stream);
+  return launch_contract(log2b, 0, MODE_IUU, a, ctx->stream);
 }
 
 extern "C" int contract_uuu(tsk_ctx* ctx, const float* FS, const float* S, const int32_t* h,
@@ -162,7 +206,7 @@ extern "C" int contract_uuu(tsk_ctx* ctx, const float* FS, const float* S, const
   a.Unext = nullptr;
   a.lam_med = lam_med;
   a.status = ctx->status;
-  return launch_contract(log2b, MODE_UUU, a, ctx->stream);
+  return launch_contract(log2b, 0, MODE_UUU, a, ctx->stream);
 }
 
 // The L power-iteration chains are independent until the selection, so they are split into
@@ -170,17 +214,31 @@ extern "C" int contract_uuu(tsk_ctx* ctx, const float* FS, const float* S, const
 // last wave of blocks and its last-arriving blocks take the medians, the other groups' steps
 // fill the idle SMs (a single B x L grid per step would leave the SMs partly idle at the end of
 // every step).  Eight groups measured at least as fast as fewer for every sketch length.
+// Alg. 1 splits each (vector, sketch) contraction's frequencies over 2^logp blocks (see
+// contract_one): smaller blocks fit more of them per SM and hide each other's barriers, but
+// every block repeats the work that grows with n (scatter, read-off, the sum of the shares).
+// The blocks' transform length M = b / 2^logp is kept at >= 8 n, >= 2^12 and <= 2^14, with at
+// most 8 blocks; measured on n = 100, 400 and 1000 for b = 2^12 .. 2^16 this choice was the
+// fastest or within 3 % of it.
+static int rpm_split_log(int log2b, int64_t n) {
+  int logm = 12;
+  while (logm < 14 && ((int64_t)1 << logm) < 8 * n) ++logm;
+  if (logm >= log2b) return 0;
+  int lp = log2b - logm;
+  if (lp > 3) lp = 3;
+  return lp;
+}
+
 static long long rpm_groups(int L) {
   return L < kCtxAuxStreams ? L : kCtxAuxStreams;
 }
 
 extern "C" int64_t robust_power_method_launches(tsk_ctx* ctx, int B, int log2b, int64_t n, int k,
                                                 int L, int T) {
-  (void)n;
   if (!ctx || k < 0 || B < 1 || L < 1 || T < 1 || log2b < 8 || log2b > 16) return -1;
   if (k == 0) return 0;
   const long long G = rpm_groups(L);
-  const int split = log2b > 14 ? 1 : 0;   // deflation adds a combine launch
+  const int split = rpm_split_log(log2b, n) > 0 ? 1 : 0;   // deflation adds a combine launch
   return 1 + (int64_t)k * (G * (T + 1) + 1 + split);
 }
 
@@ -204,7 +262,8 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
   if (!U0 || !lambda || !Vout) return TSK_EINVAL;
   // sketch lengths above 2^14 are split over P blocks per (vector, sketch): per-sketch values
   // and eigenvalues are kept as P shares, and deflation needs a [B][b] staging buffer
-  const int P = split_parts(log2b);
+  const int logp = rpm_split_log(log2b, n);
+  const int P = 1 << logp;
   const size_t need = 2 * ws_round(B * b * sizeof(float2)) + ws_round((size_t)L * B * P * n * 4) +
                       ws_round((size_t)L * B * P * 4) + ws_round(2 * (size_t)L * n * 4) +
                       ws_round((size_t)k * L * 4) + ws_round((size_t)L * 4) +
@@ -228,7 +287,7 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
   if (P == 1) {
     if ((rc = launch_fft_batched(log2b, Sw, FSw, B, 0, st)) != TSK_OK) return rc;
   } else {
-    if ((rc = launch_fft_split(log2b, Sw, FSw, B, st)) != TSK_OK) return rc;
+    if ((rc = launch_fft_split(log2b, logp, Sw, FSw, B, st)) != TSK_OK) return rc;
   }
 
   ContractArgs a{};
@@ -270,7 +329,7 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
         a.Unext = next;
         a.Vmed = nullptr;
         a.lam_med = nullptr;
-        if ((rc = launch_contract(log2b, MODE_IUU, a, gs)) != TSK_OK) return rc;
+        if ((rc = launch_contract(log2b, logp, MODE_IUU, a, gs)) != TSK_OK) return rc;
         cur = next;
       }
       // selection: lambda_tau = median_m T^(m)(u_tau, u_tau, u_tau)
@@ -278,14 +337,14 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
       a.normalize_input = 0;
       a.Unext = nullptr;
       a.lam_med = lam_med + (size_t)r * L + tau0;
-      if ((rc = launch_contract(log2b, MODE_UUU, a, gs)) != TSK_OK) return rc;
+      if ((rc = launch_contract(log2b, logp, MODE_UUU, a, gs)) != TSK_OK) return rc;
       TSK_CUDA(cudaEventRecord(ctx->ev_join[s], gs));
       TSK_CUDA(cudaStreamWaitEvent(st, ctx->ev_join[s], 0));
     }
     d.Ufinal = U_iters ? U_iters + ((size_t)r * T + (T - 1)) * L * n : Ubuf + (size_t)(T & 1) * L * n;
     d.lam_med = lam_med + (size_t)r * L;
     d.round = r;
-    if ((rc = launch_deflate(log2b, d, B, st)) != TSK_OK) return rc;
+    if ((rc = launch_deflate(log2b, logp, d, B, st)) != TSK_OK) return rc;
   }
   if (S_deflated)
     TSK_CUDA(cudaMemcpyAsync(S_deflated, Sw, B * b * sizeof(float2), cudaMemcpyDeviceToDevice, st));

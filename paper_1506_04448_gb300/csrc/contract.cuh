@@ -479,10 +479,10 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB - LOGP), 1) deflate_kern
 }
 
 // Host launchers (defined in contract.cu).
-int launch_contract(int log2b, int mode, const ContractArgs& args, cudaStream_t st);
-int launch_deflate(int log2b, const DeflateArgs& args, int B, cudaStream_t st);
-int launch_fft_split(int log2b, const float2* S, float2* FS, int B, cudaStream_t st);
-// Blocks per (vector, sketch) at sketch length 2^log2b: 1 up to 2^14, then b / 2^14.
-constexpr int split_parts(int log2b) { return log2b > 14 ? 1 << (log2b - 14) : 1; }
+// logp: the sketch's frequencies are split over 2^logp blocks per (vector, sketch); the blocks'
+// transforms (length b / 2^logp) must be 2^13 or 2^14 when logp > 0.
+int launch_contract(int log2b, int logp, int mode, const ContractArgs& args, cudaStream_t st);
+int launch_deflate(int log2b, int logp, const DeflateArgs& args, int B, cudaStream_t st);
+int launch_fft_split(int log2b, int logp, const float2* S, float2* FS, int B, cudaStream_t st);
 
 }  // namespace tsk

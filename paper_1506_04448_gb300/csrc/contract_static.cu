@@ -86,5 +86,5 @@ extern "C" int contract_iuu_static(const float* FS, const float* S, const int32_
   a.Unext = nullptr;
   a.lam_med = nullptr;
   a.status = nullptr;
-  return tsk::launch_contract(log2b, tsk::MODE_IUU, a, st);
+  return tsk::launch_contract(log2b, 0, tsk::MODE_IUU, a, st);
 }

@@ -237,8 +237,9 @@ def _run_rtpm(dev, n, k, L, T_it, B, log2b, seed, noise):
     (37, 3, 4, 6, 4, 9, 0.1),         # ragged n, even B
     (16, 2, 3, 5, 1, 8, 0.05),        # a single sketch (median of one)
     (24, 2, 3, 4, 40, 10, 0.01),      # B = 40 as in the paper's largest sketch count
-    (20, 2, 3, 4, 3, 15, 0.02),       # b = 2^15: frequencies split over 2 blocks
-    (18, 2, 2, 3, 2, 16, 0.02)])      # b = 2^16: split over 4 blocks
+    (30, 2, 3, 4, 4, 13, 0.02),       # b = 2^13: frequencies split over 2 blocks of 2^12
+    (20, 2, 3, 4, 3, 15, 0.02),       # b = 2^15: split over 8 blocks of 2^12
+    (18, 2, 2, 3, 2, 16, 0.02)])      # b = 2^16: split over 8 blocks of 2^13
 def test_rtpm_stepwise_parity(dev, n, k, L, T_it, B, log2b, noise):
     from rtpm_check import check_rtpm_stepwise
     res, Sg, ho, go, U0g, _, _ = _run_rtpm(dev, n, k, L, T_it, B, log2b, 1, noise)
