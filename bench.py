@@ -356,7 +356,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (T is 256 MB); sketch build timed after an L2 flush"},
         "sketch_contractions_per_s": value * B,
-        "roofline": {"kernel": "contract_kernel<14, MODE_IUU> (grid B x L = 10 x 50)",
+        "roofline": {"kernel": "contract_kernel<14, MODE_IUU, 2> (grid B x 4 classes x L = 2000 blocks)",
                      "bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved_tf / alu_peak,
                      "traffic": measured_traffic("contract_kernel_n400_b16384.md"),
@@ -579,7 +579,7 @@ def run_lda(args):
                        "l2": "inputs larger than L2 (1.6 GB CSR corpus)"},
             "phases_ms": {"whiten": w_ms, "whitened_m3": m3_ms, "sketch_m3": sk_ms,
                           "robust_power_method": rp_ms, "recover": rc_ms},
-            "roofline": {"kernel": "contract_kernel<14, MODE_IUU> (grid B x L = 20 x 50, n = 100)",
+            "roofline": {"kernel": "contract_kernel<14, MODE_IUU, 2> (grid B x 4 classes x L = 20 x 4 x 50, n = 100)",
                          "bound": "alu", "achieved": achieved_tf, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": achieved_tf / alu_peak, "traffic": None,
                          "launch_ms": k_ms, "flops_per_launch": flops,

@@ -135,7 +135,8 @@ int sketch_rank1(tsk_ctx* ctx, int64_t count, const float* w, const float* U, co
  *       -- the printed 1 and 1 on the outer terms give a biased estimate).
  * FS: [B][b] TSK_C64 = DFT of S; S: [B][b] TSK_C64 time-domain sketch; U: [L][n] float.
  * Vmed: [L][n] float, median over m of v^(m) (mean of the two middle values for even B).
- * Vall: optional [L][B][n] float, every v^(m) (NULL: kept in workspace only).
+ * Vall: optional [L][B][n] float, every v^(m).  Without it the call may split each sketch's
+ *   frequencies over several blocks as robust_power_method does (same result).
  * Limits: log2b in [8, 14], 1 <= B <= 64, 1 <= n <= 8192. */
 int contract_iuu(tsk_ctx* ctx, const float* FS, const float* S, const int32_t* h,
                  const uint8_t* g, int B, int log2b, const float* U, int L, int64_t n,

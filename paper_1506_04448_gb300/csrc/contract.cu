@@ -137,6 +137,22 @@ int launch_fft_batched(int log2b, const float2* in, float2* out, int B, int inve
 
 using namespace tsk;
 
+// Alg. 1 (and contract_iuu / contract_uuu without per-sketch outputs) splits each (vector, sketch) contraction's frequencies over 2^logp blocks (see
+// contract_one): smaller blocks fit more of them per SM and hide each other's barriers, but
+// every block repeats the work that grows with n (scatter, read-off, the sum of the shares).
+// The blocks' transform length M = b / 2^logp is kept at >= 8 n, >= 2^12 and <= 2^14, with at
+// most 8 blocks; measured on n = 100, 400 and 1000 for b = 2^12 .. 2^16 this choice was the
+// fastest or within 3 % of it.
+static int rpm_split_log(int log2b, int64_t n) {
+  int logm = 12;
+  while (logm < 14 && ((int64_t)1 << logm) < 8 * n) ++logm;
+  if (logm >= log2b) return 0;
+  int lp = log2b - logm;
+  if (lp > 3) lp = 3;
+  return lp;
+}
+
+
 static int check_contract_args(tsk_ctx* ctx, const float* FS, const float* S, const int32_t* h,
                                const uint8_t* g, int B, int log2b, const float* U, int L, int64_t n) {
   if (!ctx || !FS || !S || !h || !g || !U) return TSK_EINVAL;
@@ -152,14 +168,17 @@ extern "C" int contract_iuu(tsk_ctx* ctx, const float* FS, const float* S, const
   int rc = check_contract_args(ctx, FS, S, h, g, B, log2b, U, L, n);
   if (rc != TSK_OK) return rc;
   if (!Vmed) return TSK_EINVAL;
-  const size_t vall_bytes = Vall ? 0 : ws_round((size_t)L * B * n * sizeof(float));
-  const size_t need = vall_bytes + ws_round((size_t)L * B * sizeof(float)) +
+  // per-sketch values requested: one block per (vector, sketch); otherwise the split of Alg. 1
+  const int logp = Vall ? 0 : rpm_split_log(log2b, n);
+  const int P = 1 << logp;
+  const size_t vall_bytes = Vall ? 0 : ws_round((size_t)L * B * P * n * sizeof(float));
+  const size_t need = vall_bytes + ws_round((size_t)L * B * P * sizeof(float)) +
                       ws_round((size_t)L * sizeof(unsigned));
   if ((rc = tsk_ws_reserve(ctx, need)) != TSK_OK) return rc;
   WsCarve wc{static_cast<char*>(ctx->ws), 0};
   ContractArgs a{};
-  a.Vall = Vall ? Vall : wc.take<float>((size_t)L * B * n);
-  a.lam_all = wc.take<float>((size_t)L * B);
+  a.Vall = Vall ? Vall : wc.take<float>((size_t)L * B * P * n);
+  a.lam_all = wc.take<float>((size_t)L * B * P);
   a.counters = wc.take<unsigned>(L);
   TSK_CUDA(cudaMemsetAsync(a.counters, 0, L * sizeof(unsigned), ctx->stream));
   a.FS = reinterpret_cast<const float2*>(FS);
@@ -175,7 +194,7 @@ extern "C" int contract_iuu(tsk_ctx* ctx, const float* FS, const float* S, const
   a.Unext = nullptr;
   a.lam_med = nullptr;
   a.status = ctx->status;
-  return launch_contract(log2b, 0, MODE_IUU, a, ctx->stream);
+  return launch_contract(log2b, logp, MODE_IUU, a, ctx->stream);
 }
 
 extern "C" int contract_uuu(tsk_ctx* ctx, const float* FS, const float* S, const int32_t* h,
@@ -184,12 +203,14 @@ extern "C" int contract_uuu(tsk_ctx* ctx, const float* FS, const float* S, const
   int rc = check_contract_args(ctx, FS, S, h, g, B, log2b, U, L, n);
   if (rc != TSK_OK) return rc;
   if (!lam_med) return TSK_EINVAL;
-  const size_t need = (lam_all ? 0 : ws_round((size_t)L * B * sizeof(float))) +
+  const int logp = lam_all ? 0 : rpm_split_log(log2b, n);
+  const int P = 1 << logp;
+  const size_t need = (lam_all ? 0 : ws_round((size_t)L * B * P * sizeof(float))) +
                       ws_round((size_t)L * sizeof(unsigned));
   if ((rc = tsk_ws_reserve(ctx, need)) != TSK_OK) return rc;
   WsCarve wc{static_cast<char*>(ctx->ws), 0};
   ContractArgs a{};
-  a.lam_all = lam_all ? lam_all : wc.take<float>((size_t)L * B);
+  a.lam_all = lam_all ? lam_all : wc.take<float>((size_t)L * B * P);
   a.counters = wc.take<unsigned>(L);
   TSK_CUDA(cudaMemsetAsync(a.counters, 0, L * sizeof(unsigned), ctx->stream));
   a.FS = reinterpret_cast<const float2*>(FS);
@@ -206,7 +227,7 @@ extern "C" int contract_uuu(tsk_ctx* ctx, const float* FS, const float* S, const
   a.Unext = nullptr;
   a.lam_med = lam_med;
   a.status = ctx->status;
-  return launch_contract(log2b, 0, MODE_UUU, a, ctx->stream);
+  return launch_contract(log2b, logp, MODE_UUU, a, ctx->stream);
 }
 
 // The L power-iteration chains are independent until the selection, so they are split into
@@ -214,21 +235,6 @@ extern "C" int contract_uuu(tsk_ctx* ctx, const float* FS, const float* S, const
 // last wave of blocks and its last-arriving blocks take the medians, the other groups' steps
 // fill the idle SMs (a single B x L grid per step would leave the SMs partly idle at the end of
 // every step).  Eight groups measured at least as fast as fewer for every sketch length.
-// Alg. 1 splits each (vector, sketch) contraction's frequencies over 2^logp blocks (see
-// contract_one): smaller blocks fit more of them per SM and hide each other's barriers, but
-// every block repeats the work that grows with n (scatter, read-off, the sum of the shares).
-// The blocks' transform length M = b / 2^logp is kept at >= 8 n, >= 2^12 and <= 2^14, with at
-// most 8 blocks; measured on n = 100, 400 and 1000 for b = 2^12 .. 2^16 this choice was the
-// fastest or within 3 % of it.
-static int rpm_split_log(int log2b, int64_t n) {
-  int logm = 12;
-  while (logm < 14 && ((int64_t)1 << logm) < 8 * n) ++logm;
-  if (logm >= log2b) return 0;
-  int lp = log2b - logm;
-  if (lp > 3) lp = 3;
-  return lp;
-}
-
 static long long rpm_groups(int L) {
   return L < kCtxAuxStreams ? L : kCtxAuxStreams;
 }

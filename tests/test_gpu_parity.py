@@ -178,6 +178,9 @@ def test_contract_iuu_and_uuu(dev, n, log2b, B, L):
     Ud = t32(U, dev)
     Vmed, Vall = tsk.contract_iuu(FS, S, h, g, Ud, return_all=True)
     lam, lam_all = tsk.contract_uuu(FS, S, h, g, Ud, return_all=True)
+    # without per-sketch outputs the call may split each sketch's frequencies over blocks
+    Vmed_s = tsk.contract_iuu(FS, S, h, g, Ud).cpu().numpy()
+    lam_s = tsk.contract_uuu(FS, S, h, g, Ud).cpu().numpy()
     Sg = S.cpu().numpy().astype(np.complex128)
     Ug = Ud.cpu().numpy().astype(np.float64)
     Vall = Vall.cpu().numpy()
@@ -188,7 +191,9 @@ def test_contract_iuu_and_uuu(dev, n, log2b, B, L):
         for m in range(B):
             assert rel(Vall[tau, m], refs[m]) < 1e-5, (tau, m)
         assert rel(Vmed[tau].cpu().numpy(), O.median_rows(refs)) < 1e-5
+        assert rel(Vmed_s[tau], O.median_rows(refs)) < 1e-5
         scale = np.linalg.norm(refs) / np.sqrt(B)
+        assert abs(lam_s[tau] - O.median(lrefs)) < 1e-5 * max(scale, 1e-30)
         assert np.max(np.abs(lam_all[tau] - lrefs)) < 1e-5 * max(scale, 1e-30)
         assert abs(lam[tau].item() - O.median(lrefs)) < 1e-5 * max(scale, 1e-30)
         # per-sketch invariant T^(u,u,u) = <u, T^(I,u,u)> (App. B)
