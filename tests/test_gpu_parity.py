@@ -284,3 +284,32 @@ def test_argument_errors(dev):
         tsk.contract_iuu(Sbig, Sbig, h, g, torch.ones((1, 10), device=dev))
     with pytest.raises(TypeError):
         tsk.contract_iuu(S, S, h, g, torch.ones((1, 10), device=dev, dtype=torch.float64))
+
+
+def test_rtpm_captured_in_a_cuda_graph(dev):
+    """Alg. 1 enqueued once into a CUDA graph (after a warm-up call has grown the workspace and
+    created the helper streams) and replayed: every step of the replay passes the step-wise
+    oracle check."""
+    from rtpm_check import check_rtpm_stepwise
+    n, k, L, T_it, B, log2b = 40, 2, 3, 4, 4, 12
+    T, _, _ = synth.planted_symmetric(n, k, 0.02, 5)
+    U0 = t32(synth.gaussian_inits(k, L, n, 6), dev)
+    h, g = tsk.cs_hashes(5, B, log2b, [n], dev)
+    S = tsk.sketch_tensor(t32(T, dev), h, g, log2b)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        tsk.robust_power_method(S, h, g, U0, T_it, return_deflated=True, return_trace=True)
+    torch.cuda.current_stream(dev).wait_stream(side)
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        res = tsk.robust_power_method(S, h, g, U0, T_it, return_deflated=True, return_trace=True)
+    graph.replay()
+    torch.cuda.synchronize(dev)
+    tsk.check_status(dev)
+    host = {key: val.cpu().numpy() for key, val in res.items()}
+    ho, go = O.cs_hashes(5, B, log2b, [n])
+    Sg = S.cpu().numpy().astype(np.complex128)
+    U0g = U0.cpu().numpy().astype(np.float64)
+    assert check_rtpm_stepwise(host, Sg, ho[:, 0], go[:, 0], 1 << log2b, U0g, T_it) == k * T_it * L
