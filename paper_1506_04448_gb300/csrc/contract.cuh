@@ -109,26 +109,29 @@ __device__ __forceinline__ float contract_one(float2* A, float2* Eb, float* red,
       atomicAdd(slot + (gi & 1), (gi & 2) ? -x : x);
       atomicAdd(&Eb[pad_idx(hi & (hb - 1))].x, (gi & 1) ? -x * x : x * x);
     } else {
-      const float2 v = cmul(cmul_ipow(make_float2(x, 0.f), gi), unit_root_wide(tw, (part * hi) & (b - 1), b, -1));
+      // twiddles w_b^(part h) for s_u and w_(b/2)^(part (h mod b/2)) = (w_b^(part h))^2 for s_2
+      const float2 w1 = unit_root_wide(tw, (part * hi) & (b - 1), b, -1);
+      const float2 v = cmul(cmul_ipow(make_float2(x, 0.f), gi), w1);
       float* slot = reinterpret_cast<float*>(&A[pad_idx(hi & (M - 1))]);
       atomicAdd(slot, v.x);
       atomicAdd(slot + 1, v.y);
-      const int h2 = hi & (hb - 1);
       const float e = (gi & 1) ? -x * x : x * x;
-      const float2 w2 = unit_root(tw, (part * h2) & (hb - 1), hb, -1);
-      float* es = reinterpret_cast<float*>(&Eb[pad_idx(h2 & (hM - 1))]);
+      const float2 w2 = cmul(w1, w1);
+      float* es = reinterpret_cast<float*>(&Eb[pad_idx(hi & (hM - 1))]);
       atomicAdd(es, e * w2.x);
       atomicAdd(es + 1, e * w2.y);
     }
   }
   __syncthreads();
 
-  // 2. forward DFTs (the two transforms' passes interleaved).
-  block_fft_pair<LOGM, LOGM - 1, NT, -1>(A, Eb, tw);
+  // 2. forward DFTs (the two transforms' passes interleaved).  The loops below touch only each
+  // thread's own slots t + NT s (f = tid + NT s), so no barrier is needed after the transforms
+  // or between the spectral products and the inverse transforms (slot ownership, fft.cuh).
+  block_fft_pair<LOGM, LOGM - 1, NT, -1, false>(A, Eb, tw);
 
   float lam = 0.f;
   if constexpr (MODE == MODE_IUU) {
-    // 3. spectral products (each f < b/2 owns positions f and f + b/2 of A and f of Eb).
+    // 3. spectral products (each f < M/2 owns positions f and f + M/2 of A and f of Eb).
     for (int f = tid; f < hM; f += NT) {
       const float2 cu0 = cconj(A[pad_idx(f)]);
       const float2 cu1 = cconj(A[pad_idx(f + hM)]);
@@ -139,7 +142,6 @@ __device__ __forceinline__ float contract_one(float2* A, float2* Eb, float* red,
       A[pad_idx(f + hM)] = cmul(F1, cadd(cmul(cu1, cu1), cv));
       Eb[pad_idx(f)] = cadd(cmul(F0, cu0), cmul(F1, cu1));
     }
-    __syncthreads();
     // 4. inverse DFTs and hashed read-off.
     block_fft_pair<LOGM, LOGM - 1, NT, +1>(A, Eb, tw);
     for (int i = tid; i < n; i += NT) {
@@ -149,9 +151,9 @@ __device__ __forceinline__ float contract_one(float2* A, float2* Eb, float* red,
       float2 g12 = A[pad_idx(hi & (M - 1))];
       float2 g0 = Eb[pad_idx(hi & (hM - 1))];
       if constexpr (LOGP > 0) {
-        g12 = cmul(g12, unit_root_wide(tw, (part * hi) & (b - 1), b, +1));
-        const int h2 = hi & (hb - 1);
-        g0 = cmul(g0, unit_root(tw, (part * h2) & (hb - 1), hb, +1));
+        const float2 w1 = unit_root_wide(tw, (part * hi) & (b - 1), b, +1);
+        g12 = cmul(g12, w1);
+        g0 = cmul(g0, cmul(w1, w1));
       }
       float v = (re_ipow(g12, -gi) * (1.f / 6.f) + re_ipow(g0, -2 * gi) * x * (1.f / 3.f)) * inv_b;
       if (LOGP == 0 || part == 0) {

@@ -10,6 +10,12 @@
 // Pass structure (Stockham auto-sort): with NS = product of the radices already applied,
 // butterfly j reads x[j + r N/R] (r < R), multiplies element r by w_{NS R}^{DIR r (j mod NS)},
 // takes an R-point DFT and writes element r to x[(j / NS) NS R + (j mod NS) + r NS].
+//
+// Slot ownership: thread t runs butterflies j = t + q NT, so the first pass reads, and the last
+// pass (NS = N/R, j < NS) writes, exactly the slots t + NT s (s < N/NT) -- whatever the radices.
+// The last pass is therefore in place per thread and needs no barrier between its loads and
+// stores, and a pointwise step between a forward and an inverse transform that touches only the
+// thread's own slots t + NT s needs no barrier before or after it.
 #pragma once
 
 #include "common.cuh"
@@ -83,15 +89,22 @@ TSK_HD void dft_dif(float2* v) {
 }
 
 // Twiddle table: w^m for w = exp(-2 pi i / 2^15) and m < 2^15 as the product of two tables,
-// tw[m & 255] * tw[256 + (m >> 8)].  It lives in shared memory (3 KB) and is filled once per
-// block by fill_twiddles(); one lookup replaces a sincospif call per butterfly.
+// lo[m & 255] * hi[m >> 8].  It lives in shared memory (3 KB) and is filled once per block by
+// fill_twiddles(); one lookup replaces a sincospif call per butterfly.  The 256 entries of lo are
+// stored XOR-swizzled, entry i at tw_lo_slot(i) (the low four index bits XORed with the high
+// four): a Stockham pass looks up i = s k for consecutive k and a power-of-two stride s, and in
+// linear order those entries share a few banks (up to 16-way conflicts for s = 16); swizzled,
+// every distinct entry of a half-warp's lookup falls in its own bank pair.
 constexpr int kTwLog = 15;
 constexpr int kTwLo = 256;
 constexpr int kTwEntries = kTwLo + (1 << kTwLog) / kTwLo;
 
+TSK_HD constexpr int tw_lo_slot(int i) { return (i & 0xF0) | ((i ^ (i >> 4)) & 0xF); }
+
 __device__ __forceinline__ void fill_twiddles(float2* tw, int nt) {
   for (int j = threadIdx.x; j < kTwEntries; j += nt) {
-    const int m = j < kTwLo ? j : (j - kTwLo) * kTwLo;
+    // tw_lo_slot is an involution: slot j < 256 holds lo entry tw_lo_slot(j)
+    const int m = j < kTwLo ? tw_lo_slot(j) : (j - kTwLo) * kTwLo;
     float s, c;
     sincospif(-2.f * (float)m / (float)(1 << kTwLog), &s, &c);
     tw[j] = make_float2(c, s);
@@ -103,7 +116,7 @@ __device__ __forceinline__ void fill_twiddles(float2* tw, int nt) {
 TSK_HD float2 unit_root(const float2* tw, int k, int span, int dir) {
 #ifdef __CUDA_ARCH__
   const int m = k * ((1 << kTwLog) / span);
-  const float2 w = cmul(tw[m & (kTwLo - 1)], tw[kTwLo + (m >> 8)]);
+  const float2 w = cmul(tw[tw_lo_slot(m & (kTwLo - 1))], tw[kTwLo + (m >> 8)]);
   return dir > 0 ? cconj(w) : w;
 #else
   (void)tw;
@@ -194,7 +207,7 @@ struct FftPasses {
   static __device__ __forceinline__ void run(float2* x, const float2* tw) {
     float2 v[E];
     StockhamPass<N, NT, R, NS, DIR>::load_compute(x, tw, threadIdx.x, v);
-    __syncthreads();
+    if constexpr (NS * R < N) __syncthreads();       // the last pass is in place per thread
     StockhamPass<N, NT, R, NS, DIR>::store(x, threadIdx.x, v);
     __syncthreads();
     if constexpr (NS * R < N) FftPasses<N, NT, NS * R, DIR>::run(x, tw);
@@ -206,44 +219,52 @@ struct FftPasses {
 // (load, sync, store).  E's barrier also orders A's stores before A's next loads, and A's next
 // barrier orders E's stores before E's next loads, so a step costs two barriers where the two
 // transforms run one after the other would cost four.  An extra barrier is taken only when a
-// step lacks one of the two parts.  PREV_E: the previous step ended with an E part.
-template <int NA, int NE, int NT, int NSA, int NSE, int DIR, bool PREV_E = true>
+// step lacks one of the two parts.  PREV_E: the previous step ended with an E part.  A final
+// pass skips its own load/store barrier (it is in place per thread) unless that barrier also
+// orders the other transform's accesses.  FINAL_SYNC = false leaves out the closing barrier, for
+// callers that next touch only their own slots t + NT s.
+template <int NA, int NE, int NT, int NSA, int NSE, int DIR, bool PREV_E = true,
+          bool FINAL_SYNC = true>
 struct FftPair {
   static constexpr int EA = NA / NT, EE = NE / NT;
   static constexpr int RMA = EA > 16 ? 16 : EA, RME = EE > 16 ? 16 : EE;
   static constexpr bool DO_A = NSA < NA, DO_E = NSE < NE;
   static constexpr int RA = !DO_A ? 1 : (NA / NSA >= RMA ? RMA : NA / NSA);
   static constexpr int RE = !DO_E ? 1 : (NE / NSE >= RME ? RME : NE / NSE);
+  static constexpr bool A_FINAL = DO_A && NSA * RA == NA, E_FINAL = DO_E && NSE * RE == NE;
   static __device__ __forceinline__ void run(float2* xa, float2* xe, const float2* tw) {
     if constexpr (DO_A) {
       if constexpr (!PREV_E) __syncthreads();
       float2 v[EA];
       StockhamPass<NA, NT, RA, NSA, DIR>::load_compute(xa, tw, threadIdx.x, v);
-      __syncthreads();
+      // also orders E's previous stores before E's loads below
+      if constexpr (!A_FINAL || DO_E) __syncthreads();
       StockhamPass<NA, NT, RA, NSA, DIR>::store(xa, threadIdx.x, v);
     }
     if constexpr (DO_E) {
       if constexpr (!DO_A) __syncthreads();
       float2 w[EE];
       StockhamPass<NE, NT, RE, NSE, DIR>::load_compute(xe, tw, threadIdx.x, w);
-      __syncthreads();
+      // also orders A's stores above before A's next loads
+      if constexpr (!E_FINAL || (DO_A && !A_FINAL)) __syncthreads();
       StockhamPass<NE, NT, RE, NSE, DIR>::store(xe, threadIdx.x, w);
     }
     if constexpr (DO_A || DO_E) {
-      FftPair<NA, NE, NT, NSA * RA, NSE * RE, DIR, DO_E>::run(xa, xe, tw);
-    } else {
+      FftPair<NA, NE, NT, NSA * RA, NSE * RE, DIR, DO_E, FINAL_SYNC>::run(xa, xe, tw);
+    } else if constexpr (FINAL_SYNC) {
       __syncthreads();
     }
   }
 };
 
 // block_fft of two arrays at once (xa: 2^LOGA points, xe: 2^LOGE points), interleaved as above.
-template <int LOGA, int LOGE, int NT, int DIR>
+// FINAL_SYNC = false: the caller next touches only each thread's own slots t + NT s of xa and xe.
+template <int LOGA, int LOGE, int NT, int DIR, bool FINAL_SYNC = true>
 __device__ __forceinline__ void block_fft_pair(float2* xa, float2* xe, const float2* tw) {
   constexpr int NA = 1 << LOGA, NE = 1 << LOGE;
   static_assert(NA / NT >= 2 && NA / NT <= 32 && NE / NT >= 2 && NE / NT <= 32, "2..32 per thread");
   static_assert(LOGA <= kTwLog && LOGE <= kTwLog, "twiddle table covers transforms up to 2^15");
-  FftPair<NA, NE, NT, 1, 1, DIR>::run(xa, xe, tw);
+  FftPair<NA, NE, NT, 1, 1, DIR, true, FINAL_SYNC>::run(xa, xe, tw);
 }
 
 // In-place FFT of N = 2^LOGN complex values at x (padded layout) by a block of exactly NT
