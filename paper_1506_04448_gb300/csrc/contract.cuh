@@ -110,7 +110,7 @@ __device__ __forceinline__ float contract_one(float2* A, float2* Eb, float* red,
       atomicAdd(&Eb[pad_idx(hi & (hb - 1))].x, (gi & 1) ? -x * x : x * x);
     } else {
       // twiddles w_b^(part h) for s_u and w_(b/2)^(part (h mod b/2)) = (w_b^(part h))^2 for s_2
-      const float2 w1 = unit_root_wide(tw, (part * hi) & (b - 1), b, -1);
+      const float2 w1 = unit_root_direct((part * hi) & (b - 1), LOGB, -1);
       const float2 v = cmul(cmul_ipow(make_float2(x, 0.f), gi), w1);
       float* slot = reinterpret_cast<float*>(&A[pad_idx(hi & (M - 1))]);
       atomicAdd(slot, v.x);
@@ -151,7 +151,7 @@ __device__ __forceinline__ float contract_one(float2* A, float2* Eb, float* red,
       float2 g12 = A[pad_idx(hi & (M - 1))];
       float2 g0 = Eb[pad_idx(hi & (hM - 1))];
       if constexpr (LOGP > 0) {
-        const float2 w1 = unit_root_wide(tw, (part * hi) & (b - 1), b, +1);
+        const float2 w1 = unit_root_direct((part * hi) & (b - 1), LOGB, +1);
         g12 = cmul(g12, w1);
         g0 = cmul(g0, cmul(w1, w1));
       }

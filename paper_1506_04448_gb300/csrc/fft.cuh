@@ -137,6 +137,15 @@ __device__ __forceinline__ float2 unit_root_wide(const float2* tw, int k, int sp
   return cmul(w, r);
 }
 
+// exp(dir * 2 pi i * k / 2^logspan), 0 <= k < 2^logspan <= 2^16, by sincospif of the exact
+// argument 2k / 2^logspan instead of the shared table: for indices that differ randomly across a
+// warp (hashed positions) each table lookup costs several shared-memory wavefronts.
+__device__ __forceinline__ float2 unit_root_direct(int k, int logspan, int dir) {
+  float s, c;
+  sincospif((float)(dir > 0 ? 2 * k : -2 * k) / (float)(1 << logspan), &s, &c);
+  return make_float2(c, s);
+}
+
 // v[r] *= w^r, w = exp(DIR 2 pi i k / span), r = 1..R-1.  w^2, w^4, w^8 are formed by
 // squaring and the odd powers by one extra product, so at most four roundings separate any
 // power from the table value of w.
