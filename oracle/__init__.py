@@ -14,6 +14,7 @@ Modules (each function cites the passage it follows):
   rtpm     -- plain and sketched robust tensor power method (Sec. 2, Alg. 1)
   cp       -- sketched CP loss and gradient, sketched ALS update (Alg. 2, Eq. 15)
   lda      -- spectral LDA moments, whitening, whitened M3, recovery (App. D, Alg. 3)
+  orderp   -- order-p symmetric sketches, their contractions and Alg. 1 for p >= 3 (Sec. 3.3)
 
 Parity pins: every function is checked in tests/test_oracle_pins.py against facts fixed by
 the paper or by mathematics (collision-free exactness, Prop. 1, Lemma 1 unbiasedness and
@@ -33,3 +34,4 @@ from . import cp  # noqa: F401,E402
 from .cp import (cp_sketch_loss, cp_sketch_grad, cp_exact_loss, contract_ivw_mode,  # noqa: F401,E402
                  als_sketched_columns, als_solve)
 from . import lda  # noqa: F401,E402
+from . import orderp  # noqa: F401,E402
