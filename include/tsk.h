@@ -304,12 +304,62 @@ int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* h, const ui
                         double* lambda, float* Vout, int32_t* tau_star, float* S_deflated,
                         float* lam_all, float* U_iters);
 
-/* Number of kernel launches robust_power_method makes for these sizes on ctx's device (one
- * batched DFT, then per round G groups x (T power steps + 1 selection) + 1 deflation (+1 to
- * assemble the time-domain update when log2b > 14), where G = min(L, 8) is the number of
- * helper-stream groups the L chains are split into).  -1 on bad sizes. */
+/* Number of kernel launches robust_power_method makes for these sizes on ctx's device (one DFT
+ * of the sketches, then per round G groups x (T power steps + 1 selection) + 1 deflation (+1 to
+ * assemble the time-domain update when the frequencies are split over several blocks per
+ * contraction, which depends on n and b), where G = min(L, 8) is the number of helper-stream
+ * groups the L chains are split into).  -1 on bad sizes. */
 int64_t robust_power_method_launches(tsk_ctx* ctx, int B, int log2b, int64_t n, int k, int L,
                                      int T);
+
+/* ---------------------------------------------------------------- order-p symmetric sketches */
+
+/* The colliding sketch of Sec. 3.3 for symmetric tensors of order p = 3..6 (the paper states
+ * the extension to higher order without details; the readings here are this library's).
+ * Signs: sigma uniform on the m-th roots of unity, m = 4 for p = 3 and 8 for p = 4..6 (Sec. 3.3:
+ * E[sigma^k] = 0 unless m | k, so with m > p no two multisets of p indices alias).
+ * Hash (Prop. 2 with q = 2): h (2p)-wise independent, the Carter-Wegman polynomial of degree
+ * 2p - 1 over GF(2^61 - 1) with cs_hashes' coefficient stream; g from the degree-11 polynomial
+ * reduced mod m.  At p = 3 the hashes equal cs_hashes(M = 1).
+ * h: [B][n] int32 in [0, b); g: [B][n] uint8 in [0, m).  TSK_EUNSUPPORTED for p outside 3..6. */
+int cs_hashes_p(tsk_ctx* ctx, uint64_t seed, int B, int log2b, int p, int64_t n, int32_t* h,
+                uint8_t* g);
+
+/* Order-p colliding sketch (Eq. 7 with p indices) of a dense symmetric FP32 tensor T (row-major,
+ * n^p entries): S[m][t] = sum over ordered p-tuples with (h(i_1)+...+h(i_p)) mod b = t of
+ * T_{i_1..i_p} sigma(i_1)...sigma(i_p).  Every entry is read (no wedge).  S: [B][b] TSK_C64,
+ * overwritten.  Limits: p in 3..6, log2b <= 14, B <= 64, n <= 8192. */
+int sketch_tensor_p(tsk_ctx* ctx, const float* T, int p, int64_t n, const int32_t* h,
+                    const uint8_t* g, int B, int log2b, float* S);
+
+/* Sketched T(I,u,...,u) and T(u,...,u) for order p.  The colliding sketch counts each multiset
+ * of indices once per ordering, so T(u,...,u) is estimated by pairing S with the sketch of the
+ * complete homogeneous polynomial h_p = sum over partitions lambda of p of p_lambda / z_lambda,
+ * the power sum p_k being the count sketch s_k[(k h(i)) mod b] += sigma(i)^k u_i^k:
+ *   T^(u,...,u) = Re < S, sum_lambda (1/z_lambda) s_{lambda_1} * ... * s_{lambda_l} >,
+ * and T^(I,u,...,u) is its gradient divided by p (at p = 3: App. B, Eq. 13 and Eq. 14).
+ * FS = DFT of S, both [B][b] TSK_C64; U: [L][n].  Outputs (each may be NULL, not all):
+ * Vall [L][B][n] per-sketch T^(m)(I,u,...,u); Vmed [L][n] their median over the sketches;
+ * lam_all [L][B] per-sketch T^(m)(u,...,u); lam_med [L] their median.
+ * Limits: p in 3..6, log2b in [8, 12], B <= 64, n <= 8192, L <= 65535. */
+int contract_p(tsk_ctx* ctx, const float* FS, const float* S, const int32_t* h, const uint8_t* g,
+               int B, int log2b, int p, const float* U, int L, int64_t n, float* Vmed, float* Vall,
+               float* lam_med, float* lam_all);
+
+/* Alg. 1 for order p: as robust_power_method, with the power update
+ * u <- median_m T^(m)(I,u,...,u) / ||.||, the selection lambda_tau = median_m T^(m)(u,...,u),
+ * tau* = first argmax, and the deflation S <- S - lambda^ s_1^{*p} (the sketch of u^{(x)p} is the
+ * p-fold circular convolution of the count sketch s_1 of u).  Arguments and outputs as
+ * robust_power_method's; limits as contract_p's, L <= 4096, T >= 1. */
+int robust_power_method_p(tsk_ctx* ctx, const float* S, const int32_t* h, const uint8_t* g,
+                          int B, int log2b, int p, int64_t n, int k, int L, int T, const float* U0,
+                          double* lambda, float* Vout, int32_t* tau_star, float* S_deflated,
+                          float* lam_all, float* U_iters);
+
+/* Kernel launches of robust_power_method_p: one DFT of the sketches, then per round T power
+ * steps and the selection (one launch each: the contraction, whose last-arriving block per vector
+ * takes the medians) and the deflation.  -1 on bad sizes. */
+int64_t robust_power_method_p_launches(tsk_ctx* ctx, int p, int k, int T);
 
 /* ---------------------------------------------------------------- many independent problems */
 

@@ -6,12 +6,14 @@ thin binding.  Entry points: cs_hashes, sketch_tensor, sketch_fft, sketch_rank1,
 contract_uuu, robust_power_method, decompose_symmetric; asymmetric sketches: sketch_rfft,
 contract_ivw, cp_sketch_loss (+ CPSketchLoss autograd function), cp_als_solve, cp_als_step;
 many problems: BatchPlan (tsk_batch_create / tsk_batch_run); spectral LDA (Alg. 3):
-lda_m2_apply, lda_whiten, lda_whitened_m3, lda_sketch_m3, lda_recover, spectral_lda.
+lda_m2_apply, lda_whiten, lda_whitened_m3, lda_sketch_m3, lda_recover, spectral_lda; order-p
+symmetric sketches: cs_hashes_p, sketch_tensor_p, contract_p, robust_power_method_p.
 """
 from .api import (cs_hashes, sketch_tensor, sketch_fft, sketch_rank1,  # noqa: F401
                   contract_iuu, contract_uuu, robust_power_method, decompose_symmetric,
                   robust_power_method_launches, robust_power_method_asym, ctx_status, check_status, sketch_rfft,
                   contract_ivw, cp_sketch_loss, CPSketchLoss, cp_loss, cp_als_solve, cp_als_step,
                   BatchPlan, lda_m2_apply, lda_whiten, lda_whitened_m3, lda_sketch_m3,
-                  lda_recover, spectral_lda)
+                  lda_recover, spectral_lda, cs_hashes_p, sketch_tensor_p, contract_p,
+                  robust_power_method_p, robust_power_method_p_launches)
 from ._lib import TskError, LIB_PATH, load as load_library  # noqa: F401

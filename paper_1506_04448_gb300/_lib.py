@@ -48,6 +48,12 @@ SIGNATURES = {
     "robust_power_method_launches": (_I64, [_P, _I, _I, _I64, _I, _I, _I]),
     "robust_power_method_asym": (_I, [_P, _P, _P, _P, _I, _I, _I64, _I, _I, _I, _P, _P, _P, _P,
                                       _P, _P]),
+    "cs_hashes_p": (_I, [_P, _U64, _I, _I, _I, _I64, _P, _P]),
+    "sketch_tensor_p": (_I, [_P, _P, _I, _I64, _P, _P, _I, _I, _P]),
+    "contract_p": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _P, _I, _I64, _P, _P, _P, _P]),
+    "robust_power_method_p": (_I, [_P, _P, _P, _P, _I, _I, _I, _I64, _I, _I, _I, _P, _P, _P, _P,
+                                   _P, _P, _P]),
+    "robust_power_method_p_launches": (_I64, [_P, _I, _I, _I]),
     "lda_m2_apply": (_I, [_P, _P, _P, _P, _I64, _I64, _D, _P, _I, _P]),
     "lda_whiten": (_I, [_P, _P, _P, _P, _I64, _I64, _I, _D, _P, _I, _I, _P, _P, _P]),
     "lda_whitened_m3": (_I, [_P, _P, _P, _P, _I64, _I64, _P, _I, _D, _P]),

@@ -634,3 +634,99 @@ def spectral_lda(indptr, idx, cnt, V: int, k: int, alpha0: float, Omega: torch.T
     res = robust_power_method(S, h, g, U0, T)
     alpha, mu = lda_recover(W, alpha0, res["lam"], res["V"])
     return {"alpha": alpha, "mu": mu, "lam": res["lam"], "V": res["V"], "W": W, "sigma": sigma}
+
+
+# ------------------------------------------------------------------ order-p symmetric sketches
+def cs_hashes_p(seed: int, B: int, log2b: int, p: int, n: int, device="cuda"):
+    """Order-p colliding hashes: (h int32 [B][n] in [0, b), g uint8 [B][n] in [0, m)), with h
+    (2p)-wise independent and sigma = exp(2 pi i g / m), m = 4 (p = 3) or 8 (p = 4..6)."""
+    device = torch.device(device)
+    h = torch.empty((B, n), dtype=torch.int32, device=device)
+    g = torch.empty((B, n), dtype=torch.uint8, device=device)
+    rc = _lib.load().cs_hashes_p(_ctx(device), ctypes.c_uint64(seed & (2**64 - 1)), B, log2b, p, n,
+                                 _ptr(h), _ptr(g))
+    _lib.check("cs_hashes_p", rc)
+    return h, g
+
+
+def sketch_tensor_p(T: torch.Tensor, h: torch.Tensor, g: torch.Tensor, log2b: int):
+    """Order-p colliding sketches (complex64 [B][b]) of a dense symmetric float32 tensor T
+    (p = T.dim(), every entry read)."""
+    device = T.device
+    _need(T, "T", torch.float32, device)
+    _need(h, "h", torch.int32, device)
+    _need(g, "g", torch.uint8, device)
+    p, n = T.dim(), T.shape[0]
+    B = h.shape[0]
+    if h.shape != (B, n) or g.shape != (B, n) or any(d != n for d in T.shape):
+        raise ValueError("T must be n^p and h, g [B][n]")
+    S = torch.empty((B, 1 << log2b), dtype=torch.complex64, device=device)
+    rc = _lib.load().sketch_tensor_p(_ctx(device), _ptr(T.contiguous()), p, n, _ptr(h), _ptr(g), B,
+                                     log2b, _ptr(S))
+    _lib.check("sketch_tensor_p", rc)
+    return S
+
+
+def contract_p(FS: torch.Tensor, S: torch.Tensor, h: torch.Tensor, g: torch.Tensor, U: torch.Tensor,
+               p: int, per_sketch: bool = False, medians: bool = True):
+    """Sketched T(I,u,...,u) and T(u,...,u) of order p for the rows of U [L][n] against B
+    sketches (FS = DFT of S, both complex64 [B][b]).  Returns dict(Vmed [L][n], lam_med [L]
+    [, Vall [L][B][n], lam_all [L][B]]); medians=False (with per_sketch) skips the medians."""
+    if not medians and not per_sketch:
+        raise ValueError("medians=False needs per_sketch=True")
+    device = S.device
+    for t, nm in ((FS, "FS"), (S, "S")):
+        _need(t, nm, torch.complex64, device)
+    _need(U, "U", torch.float32, device)
+    B, b = S.shape
+    L, n = U.shape
+    Vmed = torch.empty((L, n), dtype=torch.float32, device=device) if medians else None
+    lam_med = torch.empty((L,), dtype=torch.float32, device=device) if medians else None
+    Vall = torch.empty((L, B, n), dtype=torch.float32, device=device) if per_sketch else None
+    lam_all = torch.empty((L, B), dtype=torch.float32, device=device) if per_sketch else None
+    rc = _lib.load().contract_p(_ctx(device), _ptr(FS), _ptr(S), _ptr(h), _ptr(g), B,
+                                b.bit_length() - 1, p, _ptr(U), L, n, _ptr(Vmed), _ptr(Vall),
+                                _ptr(lam_med), _ptr(lam_all))
+    _lib.check("contract_p", rc)
+    out = {"Vmed": Vmed, "lam_med": lam_med} if medians else {}
+    if per_sketch:
+        out["Vall"], out["lam_all"] = Vall, lam_all
+    return out
+
+
+def robust_power_method_p(S: torch.Tensor, h: torch.Tensor, g: torch.Tensor, U0: torch.Tensor,
+                          T: int, p: int, return_deflated: bool = False, return_trace: bool = False):
+    """Alg. 1 for order p on B colliding sketches S [B][b] with hashes h, g [B][n] and initial
+    vectors U0 [k][L][n].  Returns as robust_power_method."""
+    device = S.device
+    _need(S, "S", torch.complex64, device)
+    _need(h, "h", torch.int32, device)
+    _need(g, "g", torch.uint8, device)
+    _need(U0, "U0", torch.float32, device)
+    B, b = S.shape
+    k, L, n = U0.shape
+    if h.shape != (B, n) or g.shape != (B, n):
+        raise ValueError(f"h and g must have shape [{B}][{n}]")
+    lam = torch.empty((k,), dtype=torch.float64, device=device)
+    V = torch.empty((k, n), dtype=torch.float32, device=device)
+    tau = torch.empty((k,), dtype=torch.int32, device=device)
+    Sd = torch.empty_like(S) if return_deflated else None
+    lam_all = torch.empty((k, L), dtype=torch.float32, device=device) if return_trace else None
+    U_iters = (torch.empty((k, int(T), L, n), dtype=torch.float32, device=device)
+               if return_trace else None)
+    rc = _lib.load().robust_power_method_p(_ctx(device), _ptr(S), _ptr(h), _ptr(g), B,
+                                           b.bit_length() - 1, p, n, k, L, int(T), _ptr(U0),
+                                           _ptr(lam), _ptr(V), _ptr(tau), _ptr(Sd), _ptr(lam_all),
+                                           _ptr(U_iters))
+    _lib.check("robust_power_method_p", rc)
+    out = {"lam": lam, "V": V, "tau": tau}
+    if return_deflated:
+        out["S_deflated"] = Sd
+    if return_trace:
+        out["lam_all"], out["U_iters"] = lam_all, U_iters
+    return out
+
+
+def robust_power_method_p_launches(p: int, k: int, T: int, device="cuda") -> int:
+    """Kernel launches robust_power_method_p makes (the figure bench.py reports)."""
+    return int(_lib.load().robust_power_method_p_launches(_ctx(torch.device(device)), p, k, T))

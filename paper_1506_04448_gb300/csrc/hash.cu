@@ -75,7 +75,50 @@ __global__ void hash_kernel(uint64_t seed, int B, int M, int nmax, int log2b, Ha
   }
 }
 
+// Order-p colliding hashes (p = 3..6): h from the degree-(2p-1) polynomial of table 0, so that
+// h is (2p)-wise independent and H = h(i_1) + ... + h(i_p) 2-wise independent (Prop. 2 with
+// q = 2); the sign index from the degree-11 polynomial of table 1 reduced mod m, sigma uniform
+// on the m-th roots of unity with m the smallest power of two above p (E[sigma^k] = 0 unless
+// m | k, so no two distinct multisets of p indices alias, Sec. 3.3).  At p = 3 these are the
+// hashes of cs_hashes with M = 1.
+template <int DEG>
+__global__ void hash_p_kernel(uint64_t seed, int B, int n, int log2b, int mroots, int32_t* h,
+                              uint8_t* g) {
+  const long long total = (long long)B * n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % n);
+    const int m = (int)(idx / n);
+    const uint64_t hv = poly_eval<DEG>(seed, m, 0, 1, 0, (uint64_t)i);
+    const uint64_t gv = poly_eval<11>(seed, m, 0, 1, 1, (uint64_t)i);
+    h[idx] = (int32_t)(hv & ((1ull << log2b) - 1));
+    g[idx] = (uint8_t)(gv & (uint64_t)(mroots - 1));
+  }
+}
+
 }  // namespace tsk
+
+extern "C" int cs_hashes_p(tsk_ctx* ctx, uint64_t seed, int B, int log2b, int p, int64_t n,
+                           int32_t* h, uint8_t* g) {
+  if (!ctx || !h || !g) return TSK_EINVAL;
+  if (B < 1 || log2b < 1 || log2b > 24 || n < 0 || n >= (1ll << 31)) return TSK_EINVAL;
+  if (p < 3 || p > 6) return TSK_EUNSUPPORTED;
+  if (n == 0) return TSK_OK;
+  const int mroots = p < 4 ? 4 : 8;
+  const long long total = (long long)B * n;
+  const int threads = 256;
+  long long blocks = (total + threads - 1) / threads;
+  if (blocks > 65535LL * 16) blocks = 65535LL * 16;
+  const unsigned nb = (unsigned)blocks;
+  switch (p) {
+    case 3: tsk::hash_p_kernel<5><<<nb, threads, 0, ctx->stream>>>(seed, B, (int)n, log2b, mroots, h, g); break;
+    case 4: tsk::hash_p_kernel<7><<<nb, threads, 0, ctx->stream>>>(seed, B, (int)n, log2b, mroots, h, g); break;
+    case 5: tsk::hash_p_kernel<9><<<nb, threads, 0, ctx->stream>>>(seed, B, (int)n, log2b, mroots, h, g); break;
+    default: tsk::hash_p_kernel<11><<<nb, threads, 0, ctx->stream>>>(seed, B, (int)n, log2b, mroots, h, g); break;
+  }
+  TSK_CHECK_LAUNCH();
+  return TSK_OK;
+}
 
 extern "C" int cs_hashes(tsk_ctx* ctx, uint64_t seed, int B, int log2b, int M,
                          const int64_t* dims_host, int32_t* h, uint8_t* g) {

@@ -192,3 +192,17 @@ def planted_cp(dims, R: int, noise: float, seed: int, dtype=np.float32):
 def gaussian_matrix(rows: int, cols: int, seed: int) -> np.ndarray:
     """Standard Gaussian test matrix (the random start of a randomized range finder)."""
     return rng(seed).standard_normal((rows, cols))
+
+
+def planted_order4(n: int, k: int, noise: float, seed: int):
+    """Order-4 tensor sum_r lam_r a_r^{(x)4} + E (orthonormal a_r from orthonormal_columns, lam_r ~
+    U[1, 2], E i.i.d. N(0, noise^2) per entry), built in FP32 as the n^2 x n^2 matrix
+    Q diag(lam) Q^T with Q_r = vec(a_r a_r^T).  Returns (T [n][n][n][n] float32, lam, A)."""
+    r = rng(seed)
+    lam = r.uniform(1.0, 2.0, size=k)
+    A = orthonormal_columns(n, k, seed + 1)
+    Q = np.stack([np.outer(A[:, j], A[:, j]).ravel() for j in range(k)], axis=1).astype(np.float32)
+    T = (Q * lam.astype(np.float32)[None, :]) @ Q.T
+    if noise:
+        T += np.float32(noise) * rng(seed + 2).standard_normal(T.shape, dtype=np.float32)
+    return T.reshape(n, n, n, n), lam, A

@@ -57,3 +57,35 @@ def check_rtpm_stepwise(res, S0, h, g, b, U0, T_it, rounds=None, steps=None, tau
     err = np.linalg.norm(Sd - S) / np.linalg.norm(S)
     assert err <= tol_vec, err
     return checked
+
+
+def check_rtpm_p_stepwise(res, S0, h, g, b, p, U0, T_it, tol_vec=1e-4, tol_lam=1e-4):
+    """check_rtpm_stepwise for Alg. 1 of order p (oracle.orderp): every GPU iterate against the
+    oracle's order-p power update of the GPU's previous iterate, every eigenvalue estimate, the
+    first-argmax selection and the chained deflation.  h, g: [B][n]."""
+    P = O.orderp
+    lam, V, tau = res["lam"], res["V"], res["tau"]
+    lam_all = res["lam_all"]
+    U_it = res["U_iters"].astype(np.float64)
+    k, L, n = U0.shape
+    S = np.array(S0, dtype=np.complex128)
+    checked = 0
+    for r in range(k):
+        for t in range(T_it):
+            prev = normalise_rows(U0[r]) if t == 0 else U_it[r, t - 1]
+            for tu in range(L):
+                want, _ = P.power_step_p(S, prev[tu], h, g, b, p)
+                got = U_it[r, t, tu]
+                assert np.linalg.norm(got - want) <= tol_vec, (r, t, tu, np.linalg.norm(got - want))
+                checked += 1
+        want_lam = np.array([P.eigenvalue_p(S, U_it[r, T_it - 1, tu], h, g, b, p)[0] for tu in range(L)])
+        scale = max(1.0, np.max(np.abs(want_lam)))
+        assert np.max(np.abs(lam_all[r] - want_lam)) <= tol_lam * scale, (r, lam_all[r], want_lam)
+        assert want_lam[tau[r]] >= want_lam.max() - 2 * tol_lam * scale
+        assert tau[r] == int(np.argmax(lam_all[r]))
+        assert lam[r] == np.float32(lam_all[r, tau[r]])
+        np.testing.assert_array_equal(V[r], U_it[r, T_it - 1, tau[r]].astype(np.float32))
+        S = P.deflate_p(S, float(lam[r]), V[r].astype(np.float64), h, g, b, p)
+    err = np.linalg.norm(res["S_deflated"] - S) / np.linalg.norm(S)
+    assert err <= tol_vec, err
+    return checked
