@@ -1,6 +1,6 @@
 """Oracle: order-p symmetric (colliding) tensor sketches, p >= 3 -- the extension of Sec. 3.3
-that the paper states without details ("easily extended to higher order"; the recovery
-coefficients "via the Young tableaux").
+that the paper mentions without details (it attributes the higher-order recovery coefficients to
+Young tableaux).
 
 Readings (all of them this module's, written from the paper's definitions):
 
