@@ -325,12 +325,14 @@ int64_t robust_power_method_launches(tsk_ctx* ctx, int B, int log2b, int64_t n, 
 int cs_hashes_p(tsk_ctx* ctx, uint64_t seed, int B, int log2b, int p, int64_t n, int32_t* h,
                 uint8_t* g);
 
-/* Order-p colliding sketch (Eq. 7 with p indices) of a dense symmetric FP32 tensor T (row-major,
- * n^p entries): S[m][t] = sum over ordered p-tuples with (h(i_1)+...+h(i_p)) mod b = t of
- * T_{i_1..i_p} sigma(i_1)...sigma(i_p).  Every entry is read (no wedge).  S: [B][b] TSK_C64,
- * overwritten.  Limits: p in 3..6, log2b <= 14, B <= 64, n <= 8192. */
+/* Order-p colliding sketch (Eq. 7 with p indices) of a dense FP32 tensor T (row-major, n^p
+ * entries): S[m][t] = sum over ordered p-tuples with (h(i_1)+...+h(i_p)) mod b = t of
+ * T_{i_1..i_p} sigma(i_1)...sigma(i_p).  symmetric = 0: every entry is read; symmetric = 1: T is
+ * taken as symmetric and only i_1 <= ... <= i_p is read, each entry weighted by its number of
+ * orderings p!/prod(run lengths)! (n^p/p! reads; Sec. 3.3).  S: [B][b] TSK_C64, overwritten.
+ * Limits: p in 3..6, log2b <= 14, B <= 64, n <= 8192. */
 int sketch_tensor_p(tsk_ctx* ctx, const float* T, int p, int64_t n, const int32_t* h,
-                    const uint8_t* g, int B, int log2b, float* S);
+                    const uint8_t* g, int B, int log2b, int symmetric, float* S);
 
 /* Sketched T(I,u,...,u) and T(u,...,u) for order p.  The colliding sketch counts each multiset
  * of indices once per ordering, so T(u,...,u) is estimated by pairing S with the sketch of the

@@ -49,7 +49,7 @@ SIGNATURES = {
     "robust_power_method_asym": (_I, [_P, _P, _P, _P, _I, _I, _I64, _I, _I, _I, _P, _P, _P, _P,
                                       _P, _P]),
     "cs_hashes_p": (_I, [_P, _U64, _I, _I, _I, _I64, _P, _P]),
-    "sketch_tensor_p": (_I, [_P, _P, _I, _I64, _P, _P, _I, _I, _P]),
+    "sketch_tensor_p": (_I, [_P, _P, _I, _I64, _P, _P, _I, _I, _I, _P]),
     "contract_p": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _P, _I, _I64, _P, _P, _P, _P]),
     "robust_power_method_p": (_I, [_P, _P, _P, _P, _I, _I, _I, _I64, _I, _I, _I, _P, _P, _P, _P,
                                    _P, _P, _P]),

@@ -649,9 +649,11 @@ def cs_hashes_p(seed: int, B: int, log2b: int, p: int, n: int, device="cuda"):
     return h, g
 
 
-def sketch_tensor_p(T: torch.Tensor, h: torch.Tensor, g: torch.Tensor, log2b: int):
-    """Order-p colliding sketches (complex64 [B][b]) of a dense symmetric float32 tensor T
-    (p = T.dim(), every entry read)."""
+def sketch_tensor_p(T: torch.Tensor, h: torch.Tensor, g: torch.Tensor, log2b: int,
+                    symmetric: bool = False):
+    """Order-p colliding sketches (complex64 [B][b]) of a dense float32 tensor T (p = T.dim()).
+    symmetric=True reads only i_1 <= ... <= i_p with multinomial weights (T must be symmetric);
+    otherwise every entry is read."""
     device = T.device
     _need(T, "T", torch.float32, device)
     _need(h, "h", torch.int32, device)
@@ -662,7 +664,7 @@ def sketch_tensor_p(T: torch.Tensor, h: torch.Tensor, g: torch.Tensor, log2b: in
         raise ValueError("T must be n^p and h, g [B][n]")
     S = torch.empty((B, 1 << log2b), dtype=torch.complex64, device=device)
     rc = _lib.load().sketch_tensor_p(_ctx(device), _ptr(T.contiguous()), p, n, _ptr(h), _ptr(g), B,
-                                     log2b, _ptr(S))
+                                     log2b, int(bool(symmetric)), _ptr(S))
     _lib.check("sketch_tensor_p", rc)
     return S
 

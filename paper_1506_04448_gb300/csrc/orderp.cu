@@ -178,6 +178,88 @@ __global__ void __launch_bounds__(256) sketch_p_kernel(const float* T, int n, in
   }
 }
 
+// Wedge-only build for a symmetric tensor: only sorted tuples i_1 <= ... <= i_p, each weighted by
+// its number of orderings kappa = p! / prod(run lengths)! (Sec. 3.3: symmetric entries collide, so
+// reading one per multiset suffices; kappa in {1, 3, 6} at p = 3).  A warp takes a sorted prefix
+// (i_1..i_{p-2}) (flat index over n^{p-2}, unsorted ones skipped), loops i_{p-1} >= i_{p-2}, and its
+// lanes take i_p >= i_{p-1}, a contiguous segment of the row.
+__global__ void __launch_bounds__(256) sketch_p_wedge_kernel(const float* T, int n, int p,
+                                                             long long prefixes, const int32_t* h,
+                                                             const uint8_t* g, int log2b, int mroots,
+                                                             float2* S) {
+  extern __shared__ float2 hist[];
+  const int b = 1 << log2b, m = blockIdx.y;
+  int* hs = reinterpret_cast<int*>(hist + b);
+  int* gs = hs + n;
+  const int32_t* hm = h + (size_t)m * n;
+  const uint8_t* gm = g + (size_t)m * n;
+  for (int t = threadIdx.x; t < b; t += blockDim.x) hist[t] = make_float2(0.f, 0.f);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    hs[i] = hm[i] & (b - 1);
+    gs[i] = gm[i] & (mroots - 1);
+  }
+  __syncthreads();
+  float fact[kMaxOrder + 1];
+  fact[0] = 1.f;
+  for (int j = 1; j <= kMaxOrder; ++j) fact[j] = fact[j - 1] * (float)j;
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long q0 = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); q0 < prefixes;
+       q0 += warps) {
+    // digits of q0 in base n, most significant first = i_1 .. i_{p-2}; skip unsorted prefixes
+    int idx[kMaxOrder];
+    long long q = q0;
+    for (int j = p - 3; j >= 0; --j) {
+      idx[j] = (int)(q % n);
+      q /= n;
+    }
+    bool sorted = true;
+    for (int j = 1; j < p - 2; ++j) sorted &= idx[j - 1] <= idx[j];
+    if (!sorted) continue;
+    int hp = 0, gp = 0;
+    float denom = 1.f;       // product of factorials of the prefix's runs except the last
+    int run = 1;
+    for (int j = 0; j < p - 2; ++j) {
+      hp += hs[idx[j]];
+      gp += gs[idx[j]];
+      if (j > 0) {
+        if (idx[j] == idx[j - 1]) {
+          ++run;
+        } else {
+          denom *= fact[run];
+          run = 1;
+        }
+      }
+    }
+    const int v = idx[p - 3];
+    long long base = 0;
+    for (int j = 0; j < p - 2; ++j) base = base * n + idx[j];
+    for (int x = v; x < n; ++x) {
+      const float* row = T + (base * n + x) * n;
+      const int hx = hp + hs[x], gx = gp + gs[x];
+      for (int y = x + lane; y < n; y += 32) {
+        float dd;
+        if (x == v) dd = (y == x) ? denom * fact[run + 2] : denom * fact[run + 1];
+        else dd = (y == x) ? denom * fact[run] * 2.f : denom * fact[run];
+        const float kappa = fact[p] / dd;
+        const float2 val = cscale(root_of_unity(gx + gs[y], mroots), kappa * __ldg(row + y));
+        float* slot = reinterpret_cast<float*>(&hist[(hx + hs[y]) & (b - 1)]);
+        atomicAdd(slot, val.x);
+        atomicAdd(slot + 1, val.y);
+      }
+    }
+  }
+  __syncthreads();
+  float2* Sm = S + (size_t)m * b;
+  for (int t = threadIdx.x; t < b; t += blockDim.x) {
+    const float2 val = hist[t];
+    if (val.x != 0.f || val.y != 0.f) {
+      atomicAdd(&Sm[t].x, val.x);
+      atomicAdd(&Sm[t].y, val.y);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ contraction
 struct PArgs {
   const float2* FS;      // [B][b]
@@ -478,7 +560,7 @@ static int check_order_p(int p, int B, int log2b, int64_t n) {
 }
 
 extern "C" int sketch_tensor_p(tsk_ctx* ctx, const float* T, int p, int64_t n, const int32_t* h,
-                               const uint8_t* g, int B, int log2b, float* S) {
+                               const uint8_t* g, int B, int log2b, int symmetric, float* S) {
   if (!ctx || !T || !h || !g || !S) return TSK_EINVAL;
   if (B < 1 || n < 1 || log2b < 1 || log2b > 24) return TSK_EINVAL;
   if (p < 3 || p > kMaxOrder || log2b > 14 || B > kMaxB || n > 8192) return TSK_EUNSUPPORTED;
@@ -492,12 +574,21 @@ extern "C" int sketch_tensor_p(tsk_ctx* ctx, const float* T, int p, int64_t n, c
   const size_t smem = b * sizeof(float2) + 2 * (size_t)n * sizeof(int);
   if (smem > kSketchPSmemMax) return TSK_EUNSUPPORTED;
   // the limit is set once per device, so to the largest size any call may need
-  TSK_CUDA(tsk_smem_attr<sketch_p_kernel>(kSketchPSmemMax));
-  long long blocks = (rows + 7) / 8;                  // 8 warps of 256 threads, a row each
   const long long cap = 4 * 152 / B + 1;              // ~4 blocks per SM over all sketches
-  if (blocks > cap) blocks = cap;
-  sketch_p_kernel<<<dim3((unsigned)blocks, B), 256, smem, ctx->stream>>>(
-      T, (int)n, p, rows, h, g, log2b, p < 4 ? 4 : 8, reinterpret_cast<float2*>(S));
+  if (symmetric) {
+    const long long prefixes = rows / n;              // n^(p-2) flat prefixes
+    long long blocks = (prefixes + 7) / 8;            // 8 warps of 256 threads, a prefix each
+    if (blocks > cap) blocks = cap;
+    TSK_CUDA(tsk_smem_attr<sketch_p_wedge_kernel>(kSketchPSmemMax));
+    sketch_p_wedge_kernel<<<dim3((unsigned)blocks, B), 256, smem, ctx->stream>>>(
+        T, (int)n, p, prefixes, h, g, log2b, p < 4 ? 4 : 8, reinterpret_cast<float2*>(S));
+  } else {
+    long long blocks = (rows + 7) / 8;                // 8 warps of 256 threads, a row each
+    if (blocks > cap) blocks = cap;
+    TSK_CUDA(tsk_smem_attr<sketch_p_kernel>(kSketchPSmemMax));
+    sketch_p_kernel<<<dim3((unsigned)blocks, B), 256, smem, ctx->stream>>>(
+        T, (int)n, p, rows, h, g, log2b, p < 4 ? 4 : 8, reinterpret_cast<float2*>(S));
+  }
   TSK_CHECK_LAUNCH();
   return TSK_OK;
 }

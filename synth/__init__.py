@@ -195,14 +195,21 @@ def gaussian_matrix(rows: int, cols: int, seed: int) -> np.ndarray:
 
 
 def planted_order4(n: int, k: int, noise: float, seed: int):
-    """Order-4 tensor sum_r lam_r a_r^{(x)4} + E (orthonormal a_r from orthonormal_columns, lam_r ~
-    U[1, 2], E i.i.d. N(0, noise^2) per entry), built in FP32 as the n^2 x n^2 matrix
-    Q diag(lam) Q^T with Q_r = vec(a_r a_r^T).  Returns (T [n][n][n][n] float32, lam, A)."""
+    """Symmetric order-4 tensor sum_r lam_r a_r^{(x)4} + E (orthonormal a_r from
+    orthonormal_columns, lam_r ~ U[1, 2]), the signal built in FP32 as the n^2 x n^2 matrix
+    Q diag(lam) Q^T with Q_r = vec(a_r a_r^T); E = noise times the average of an i.i.d. N(0, 1)
+    tensor over the 24 permutations of its modes (symmetric; an entry with four distinct indices
+    has std noise / sqrt(24)).  Returns (T [n][n][n][n] float32, lam, A)."""
+    import itertools
     r = rng(seed)
     lam = r.uniform(1.0, 2.0, size=k)
     A = orthonormal_columns(n, k, seed + 1)
     Q = np.stack([np.outer(A[:, j], A[:, j]).ravel() for j in range(k)], axis=1).astype(np.float32)
-    T = (Q * lam.astype(np.float32)[None, :]) @ Q.T
+    T = ((Q * lam.astype(np.float32)[None, :]) @ Q.T).reshape(n, n, n, n)
     if noise:
-        T += np.float32(noise) * rng(seed + 2).standard_normal(T.shape, dtype=np.float32)
-    return T.reshape(n, n, n, n), lam, A
+        G = rng(seed + 2).standard_normal((n, n, n, n), dtype=np.float32)
+        E = np.zeros_like(G)
+        for q in itertools.permutations(range(4)):
+            E += G.transpose(q)
+        T += np.float32(noise / 24.0) * E
+    return T, lam, A

@@ -67,6 +67,25 @@ def test_sketch_tensor_p(dev, p, n, B, log2b):
         assert rel(S[m], P.sketch_sym_p(T32, ho[m], go[m], 1 << log2b, p)) < 1e-5, m
 
 
+@pytest.mark.parametrize("p,n,B,log2b", [(3, 13, 2, 9), (4, 9, 3, 10), (5, 7, 2, 8), (6, 5, 2, 12),
+                                         (4, 40, 2, 12), (3, 1, 1, 8)])
+def test_sketch_tensor_p_symmetric_wedge(dev, p, n, B, log2b):
+    """The wedge-only build of a symmetric tensor equals the definition (all ordered tuples) and
+    the GPU's full-read build."""
+    X = synth.rng(60 + p).standard_normal((n,) * p)
+    T = sum(np.transpose(X, q) for q in itertools.permutations(range(p))) / np.prod(range(1, p + 1))
+    h, g = tsk.cs_hashes_p(15 + p, B, log2b, p, n, dev)
+    Td = t32(T, dev)
+    Sw = tsk.sketch_tensor_p(Td, h, g, log2b, symmetric=True).cpu().numpy()
+    Sf = tsk.sketch_tensor_p(Td, h, g, log2b).cpu().numpy()
+    ho, go = P.cs_hashes_p(15 + p, B, log2b, p, n)
+    T32 = Td.cpu().numpy().astype(np.float64)
+    for m in range(B):
+        ref = P.sketch_sym_p(T32, ho[m], go[m], 1 << log2b, p)
+        assert rel(Sw[m], ref) < 1e-5, m
+        assert rel(Sw[m], Sf[m]) < 1e-5, m
+
+
 @pytest.mark.parametrize("p,n,B,L,log2b", [(3, 37, 3, 2, 10), (4, 37, 4, 3, 8), (4, 100, 5, 2, 12),
                                            (5, 33, 3, 2, 11), (6, 20, 2, 2, 12), (6, 5, 40, 1, 9)])
 def test_contract_p(dev, p, n, B, L, log2b):
