@@ -959,8 +959,9 @@ def run_orderp(args):
             "recovery": {"min_alignment": float(best.min()), "mean_alignment": float(best.mean())},
             "roofline": {"kernel": "contract_p_kernel<12, 4> (grid B x L = 300 blocks)", "bound": "alu",
                          "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                         "frac": achieved / alu_peak, "traffic": None,
-                         "traffic_note": "no ncu DRAM capture of this kernel (the sketches are L2-resident)",
+                         "frac": achieved / alu_peak,
+                         "traffic": measured_traffic("contract_p_kernel_order4_n100_b4096.md"),
+                         "traffic_note": "DRAM bytes per launch from the ncu capture in profiles/ (null if the kernel changed since)",
                          "launch_ms": k_ms, "flops_per_launch": flops,
                          "flops_basis": "2 (p-1) length-b FFTs x 5 b log2 b per sketch-contraction",
                          "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz"},

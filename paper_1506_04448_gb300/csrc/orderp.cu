@@ -17,13 +17,11 @@
 //                   G_k = F^-1-unnormalised(FS conj(F R_k)), F R_k = sum over lambda containing k of
 //                   (m_k(lambda) / z_lambda) prod over lambda's other parts of F(s_part).
 // At p = 3 these are App. B's Eq. 13 and Eq. 14 (coefficients 1/6, 1/6, 1/3, 1/3).  The
-// partitions are enumerated on the host (partition_terms) and passed to the kernel as a table.
+// partitions are enumerated at compile time (compile_terms).
 //
 // Deflation: the sketch of u^{(x)p} is the p-fold convolution of s_1, so FS -= lambda (F s_1)^p
 // and S -= F^-1 of the same.
 #include <stdio.h>
-
-#include <vector>
 
 #include "contract.cuh"
 
@@ -34,73 +32,80 @@ constexpr int kMaxTerms = 48;
 // dynamic shared memory of sketch_p_kernel: the b <= 2^14 histogram and two n <= 8192 tables
 constexpr size_t kSketchPSmemMax = ((size_t)1 << 14) * sizeof(float2) + 2 * (size_t)8192 * sizeof(int);
 
-struct PTerm {
-  float coef;
-  int8_t target;              // 0: a term of Y; k in 1..p-1: a term of F R_k
-  int8_t nparts;
-  int8_t parts[kMaxOrder];    // parts < p (indices of the power-sum spectra)
-};
-struct PTerms {
+// The estimators' term table for order P, built at compile time (the kernel unrolls it, so every
+// product is a chain of complex multiplications on fixed registers): for each partition lambda of
+// P other than (P), a term 1/z_lambda of Y over all of lambda's parts; for each part size k < P
+// in lambda, a term m_k(lambda)/z_lambda of F R_k over lambda's other parts.  Partitions of P are
+// enumerated in reverse lexicographic order (the classic successor rule: strip trailing ones,
+// decrement the last part above one, refill with copies of it and the remainder).
+template <int P>
+struct CTerms {
+  float coef[kMaxTerms];
+  int target[kMaxTerms];
+  int nparts[kMaxTerms];
+  int parts[kMaxTerms][kMaxOrder];
   int count;
-  PTerm t[kMaxTerms];
 };
 
-// Host: the term table of the estimators above for order p.
-static void enumerate_partitions(int rest, int largest, std::vector<int>& cur,
-                                 std::vector<std::vector<int>>& out) {
-  if (rest == 0) {
-    out.push_back(cur);
-    return;
-  }
-  for (int part = rest < largest ? rest : largest; part >= 1; --part) {
-    cur.push_back(part);
-    enumerate_partitions(rest - part, part, cur, out);
-    cur.pop_back();
-  }
-}
-
-static double z_lambda(const std::vector<int>& lam) {
-  double z = 1.0;
-  int mult[kMaxOrder + 1] = {0};
-  for (int x : lam) ++mult[x];
-  for (int k = 1; k <= kMaxOrder; ++k)
-    for (int j = 1; j <= mult[k]; ++j) z *= (double)k * (double)j;   // k^{m_k} m_k!
-  return z;
-}
-
-static int partition_terms(int p, PTerms* out) {
-  std::vector<std::vector<int>> parts;
-  std::vector<int> cur;
-  enumerate_partitions(p, p, cur, parts);
-  out->count = 0;
-  auto add = [&](double coef, int target, const std::vector<int>& ps) {
-    if (out->count >= kMaxTerms) return false;
-    PTerm& t = out->t[out->count++];
-    t.coef = (float)coef;
-    t.target = (int8_t)target;
-    t.nparts = (int8_t)ps.size();
-    for (int j = 0; j < kMaxOrder; ++j) t.parts[j] = j < (int)ps.size() ? (int8_t)ps[j] : 0;
-    return true;
-  };
-  for (const auto& lam : parts) {
-    const double z = z_lambda(lam);
-    if (!(lam.size() == 1 && lam[0] == p))
-      if (!add(1.0 / z, 0, lam)) return TSK_EUNSUPPORTED;
-    for (int k = 1; k < p; ++k) {
-      int mk = 0;
-      for (int x : lam) mk += (x == k);
-      if (mk == 0) continue;
-      std::vector<int> rest = lam;
-      for (size_t j = 0; j < rest.size(); ++j)
-        if (rest[j] == k) {
-          rest.erase(rest.begin() + j);
-          break;
-        }
-      if (!add((double)mk / z, k, rest)) return TSK_EUNSUPPORTED;
+template <int P>
+constexpr CTerms<P> compile_terms() {
+  CTerms<P> out{};
+  out.count = 0;
+  int a[kMaxOrder + 1] = {};
+  int len = 1;
+  a[0] = P;
+  while (true) {
+    // z_lambda = prod_k k^{m_k} m_k! for the partition a[0..len)
+    int mult[kMaxOrder + 1] = {};
+    for (int j = 0; j < len; ++j) ++mult[a[j]];
+    long long z = 1;
+    for (int k = 1; k <= P; ++k)
+      for (int j = 1; j <= mult[k]; ++j) z *= (long long)k * j;
+    if (!(len == 1 && a[0] == P)) {
+      out.coef[out.count] = 1.0f / (float)z;
+      out.target[out.count] = 0;
+      out.nparts[out.count] = len;
+      for (int j = 0; j < len; ++j) out.parts[out.count][j] = a[j];
+      ++out.count;
     }
+    for (int k = 1; k < P; ++k) {
+      if (mult[k] == 0) continue;
+      out.coef[out.count] = (float)mult[k] / (float)z;
+      out.target[out.count] = k;
+      int c = 0;
+      bool dropped = false;
+      for (int j = 0; j < len; ++j) {
+        if (!dropped && a[j] == k) {
+          dropped = true;
+          continue;
+        }
+        out.parts[out.count][c++] = a[j];
+      }
+      out.nparts[out.count] = c;
+      ++out.count;
+    }
+    int rem = 0;
+    while (len > 0 && a[len - 1] == 1) {
+      ++rem;
+      --len;
+    }
+    if (len == 0) break;
+    a[len - 1] -= 1;
+    ++rem;
+    const int x = a[len - 1];
+    while (rem > x) {
+      a[len++] = x;
+      rem -= x;
+    }
+    a[len++] = rem;
   }
-  return TSK_OK;
+  return out;
 }
+
+template <int P>
+struct TermTable {
+  static constexpr CTerms<P> value = compile_terms<P>();
+};
 
 // exp(2 pi i j / m) for m in {4, 8} (the sign roots), j taken mod m.
 __device__ __forceinline__ float2 root_of_unity(int j, int m) {
@@ -115,15 +120,6 @@ __device__ __forceinline__ float2 root_of_unity(int j, int m) {
     case 6: return make_float2(0.f, -1.f);
     default: return make_float2(TSK_R2, -TSK_R2);
   }
-}
-
-template <int P>
-__device__ __forceinline__ float2 pick(const float2 (&U)[P], int k) {
-  float2 r = U[0];
-#pragma unroll
-  for (int q = 1; q < P; ++q)
-    if (q == k) r = U[q];
-  return r;
 }
 
 // ------------------------------------------------------------------ build
@@ -300,7 +296,7 @@ __device__ __forceinline__ void power_sum_ffts(float2* X, const float2* tw) {
 // T^(m)(u_tau,...,u_tau) into lam_all[tau][m] (formulas at the top of this file).
 template <int LOGB, int P>
 __global__ void __launch_bounds__(threads_for_logb(LOGB), (contract_p_min_blocks<LOGB, P>()))
-    contract_p_kernel(PArgs a, PTerms terms) {
+    contract_p_kernel(PArgs a) {
   constexpr int b = 1 << LOGB;
   constexpr int NT = threads_for_logb(LOGB);
   constexpr int m_roots = P < 4 ? 4 : 8;
@@ -361,17 +357,15 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB), (contract_p_min_blocks
     float2 R[P];
 #pragma unroll
     for (int k = 0; k < P; ++k) R[k] = make_float2(0.f, 0.f);
-    for (int q = 0; q < terms.count; ++q) {
-      const PTerm& t = terms.t[q];
-      float2 prod = make_float2(t.coef, 0.f);
-      for (int j = 0; j < t.nparts; ++j) prod = cmul(prod, pick<P>(U, t.parts[j]));
-      if (t.target == 0) {
-        Y = cadd(Y, prod);
-      } else {
+    constexpr CTerms<P> tt = TermTable<P>::value;
 #pragma unroll
-        for (int k = 1; k < P; ++k)
-          if (k == t.target) R[k] = cadd(R[k], prod);
-      }
+    for (int q = 0; q < tt.count; ++q) {
+      float2 prod = U[tt.parts[q][0]];
+#pragma unroll
+      for (int j = 1; j < tt.nparts[q]; ++j) prod = cmul(prod, U[tt.parts[q][j]]);
+      prod = cscale(prod, tt.coef[q]);
+      if (tt.target[q] == 0) Y = cadd(Y, prod);
+      else R[tt.target[q]] = cadd(R[tt.target[q]], prod);
     }
     const float2 F = __ldcg(FSm + f);
     lam += F.x * Y.x + F.y * Y.y;                 // Re(F conj(Y))
@@ -476,34 +470,33 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB), 1) deflate_p_kernel(
 }
 
 template <int LOGB, int P>
-static int launch_contract_p_t(const PArgs& a, const PTerms& terms, int L, cudaStream_t st) {
+static int launch_contract_p_t(const PArgs& a, int L, cudaStream_t st) {
   constexpr size_t smem = contract_p_smem<LOGB>(P);
   static_assert(contract_p_smem<LOGB>(P) <= 227 * 1024, "transform buffers exceed shared memory");
   TSK_CUDA(tsk_smem_attr<contract_p_kernel<LOGB, P>>(smem));
-  contract_p_kernel<LOGB, P><<<dim3(a.B, L), threads_for_logb(LOGB), smem, st>>>(a, terms);
+  contract_p_kernel<LOGB, P><<<dim3(a.B, L), threads_for_logb(LOGB), smem, st>>>(a);
   TSK_CHECK_LAUNCH();
   return TSK_OK;
 }
 
 template <int LOGB>
-static int launch_contract_p_b(int p, const PArgs& a, const PTerms& terms, int L, cudaStream_t st) {
+static int launch_contract_p_b(int p, const PArgs& a, int L, cudaStream_t st) {
   switch (p) {
-    case 3: return launch_contract_p_t<LOGB, 3>(a, terms, L, st);
-    case 4: return launch_contract_p_t<LOGB, 4>(a, terms, L, st);
-    case 5: return launch_contract_p_t<LOGB, 5>(a, terms, L, st);
-    case 6: return launch_contract_p_t<LOGB, 6>(a, terms, L, st);
+    case 3: return launch_contract_p_t<LOGB, 3>(a, L, st);
+    case 4: return launch_contract_p_t<LOGB, 4>(a, L, st);
+    case 5: return launch_contract_p_t<LOGB, 5>(a, L, st);
+    case 6: return launch_contract_p_t<LOGB, 6>(a, L, st);
     default: return TSK_EUNSUPPORTED;
   }
 }
 
-static int launch_contract_p(int log2b, int p, const PArgs& a, const PTerms& terms, int L,
-                             cudaStream_t st) {
+static int launch_contract_p(int log2b, int p, const PArgs& a, int L, cudaStream_t st) {
   switch (log2b) {
-    case 8: return launch_contract_p_b<8>(p, a, terms, L, st);
-    case 9: return launch_contract_p_b<9>(p, a, terms, L, st);
-    case 10: return launch_contract_p_b<10>(p, a, terms, L, st);
-    case 11: return launch_contract_p_b<11>(p, a, terms, L, st);
-    case 12: return launch_contract_p_b<12>(p, a, terms, L, st);
+    case 8: return launch_contract_p_b<8>(p, a, L, st);
+    case 9: return launch_contract_p_b<9>(p, a, L, st);
+    case 10: return launch_contract_p_b<10>(p, a, L, st);
+    case 11: return launch_contract_p_b<11>(p, a, L, st);
+    case 12: return launch_contract_p_b<12>(p, a, L, st);
     default: return TSK_EUNSUPPORTED;
   }
 }
@@ -602,8 +595,6 @@ extern "C" int contract_p(tsk_ctx* ctx, const float* FS, const float* S, const i
   int rc = check_order_p(p, B, log2b, n);
   if (rc != TSK_OK) return rc;
   if (L > 65535) return TSK_EUNSUPPORTED;
-  PTerms terms;
-  if ((rc = partition_terms(p, &terms)) != TSK_OK) return rc;
   const bool medians = Vmed || lam_med;
   const size_t need = (Vall ? 0 : ws_round((size_t)L * B * n * sizeof(float))) +
                       (lam_all ? 0 : ws_round((size_t)L * B * sizeof(float))) +
@@ -628,7 +619,7 @@ extern "C" int contract_p(tsk_ctx* ctx, const float* FS, const float* S, const i
     a.Vmed = Vmed;
     a.lam_med = lam_med;
   }
-  return launch_contract_p(log2b, p, a, terms, L, ctx->stream);
+  return launch_contract_p(log2b, p, a, L, ctx->stream);
 }
 
 extern "C" int64_t robust_power_method_p_launches(tsk_ctx* ctx, int p, int k, int T) {
@@ -654,8 +645,6 @@ extern "C" int robust_power_method_p(tsk_ctx* ctx, const float* S, const int32_t
     return TSK_OK;
   }
   if (!U0 || !lambda || !Vout) return TSK_EINVAL;
-  PTerms terms;
-  if ((rc = partition_terms(p, &terms)) != TSK_OK) return rc;
   const size_t need = 2 * ws_round((size_t)B * b * sizeof(float2)) +
                       ws_round((size_t)L * B * n * 4) + ws_round((size_t)L * B * 4) +
                       ws_round(2 * (size_t)L * n * 4) + ws_round((size_t)k * L * 4) +
@@ -693,14 +682,14 @@ extern "C" int robust_power_method_p(tsk_ctx* ctx, const float* S, const int32_t
       a.Vmed = nullptr;
       a.Unext = next;
       a.lam_med = nullptr;
-      if ((rc = launch_contract_p(log2b, p, a, terms, L, st)) != TSK_OK) return rc;
+      if ((rc = launch_contract_p(log2b, p, a, L, st)) != TSK_OK) return rc;
       cur = next;
     }
     a.U = cur;
     a.normalize_input = 0;
     a.Unext = nullptr;
     a.lam_med = lam_med + (size_t)r * L;
-    if ((rc = launch_contract_p(log2b, p, a, terms, L, st)) != TSK_OK) return rc;
+    if ((rc = launch_contract_p(log2b, p, a, L, st)) != TSK_OK) return rc;
     if ((rc = launch_deflate_p(log2b, p, FSw, Sw, h, g, (int)n, L, cur, lam_med + (size_t)r * L, r,
                                lambda, Vout, tau_star, B, st)) != TSK_OK)
       return rc;
