@@ -567,7 +567,7 @@ extern "C" int sketch_tensor_p(tsk_ctx* ctx, const float* T, int p, int64_t n, c
   const size_t smem = b * sizeof(float2) + 2 * (size_t)n * sizeof(int);
   if (smem > kSketchPSmemMax) return TSK_EUNSUPPORTED;
   // the limit is set once per device, so to the largest size any call may need
-  const long long cap = 4 * 152 / B + 1;              // ~4 blocks per SM over all sketches
+  const long long cap = 4LL * ctx->num_sms / B + 1;   // ~4 blocks per SM over all sketches
   if (symmetric) {
     const long long prefixes = rows / n;              // n^(p-2) flat prefixes
     long long blocks = (prefixes + 7) / 8;            // 8 warps of 256 threads, a prefix each
