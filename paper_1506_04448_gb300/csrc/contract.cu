@@ -234,7 +234,8 @@ extern "C" int contract_uuu(tsk_ctx* ctx, const float* FS, const float* S, const
 // G = min(L, 8) groups, each enqueued on its own stream: while one group's step finishes its
 // last wave of blocks and its last-arriving blocks take the medians, the other groups' steps
 // fill the idle SMs (a single B x L grid per step would leave the SMs partly idle at the end of
-// every step).  Eight groups measured at least as fast as fewer for every sketch length.
+// every step).  Eight groups measured at least as fast as fewer for every sketch length, and
+// sixteen were 11 % slower for n = 400, b = 2^14, L = 50.
 static long long rpm_groups(int L) {
   return L < kCtxAuxStreams ? L : kCtxAuxStreams;
 }
