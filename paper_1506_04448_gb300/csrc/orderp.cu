@@ -19,6 +19,9 @@
 // At p = 3 these are App. B's Eq. 13 and Eq. 14 (coefficients 1/6, 1/6, 1/3, 1/3).  The
 // partitions are enumerated at compile time (compile_terms).
 //
+// s_k for even k lives on even positions only, so it is transformed at length b/2 and its
+// spectral product folded to b/2 before the inverse (xlen, power_sum_ffts).
+//
 // Deflation: the sketch of u^{(x)p} is the p-fold convolution of s_1, so FS -= lambda (F s_1)^p
 // and S -= F^-1 of the same.
 #include <stdio.h>
@@ -273,23 +276,38 @@ struct PArgs {
   float* lam_med;        // [L] median of lam_all, or NULL
 };
 
+// Shared-memory layout of the power-sum sketches: s_k for odd k has length b; for even k it lives
+// on even positions only (k h mod b is even), so it is kept at half length, e[(k/2) h mod b/2],
+// with F s_k[f] = DFT_{b/2}(e)[f mod b/2]; its inverse is read only at even positions too, so the
+// spectrum is folded to b/2 before it (as for the length-b/2 sketch of the order-3 kernels).
+template <int LOGB>
+constexpr int xlen(int k) {
+  return (k & 1) ? padded_len(1 << LOGB) : padded_len(1 << (LOGB - 1));
+}
+template <int LOGB>
+constexpr int xoff(int k) {      // offset of s_k (k >= 1); xoff(p) is the total
+  int o = 0;
+  for (int j = 1; j < k; ++j) o += xlen<LOGB>(j);
+  return o;
+}
 template <int LOGB>
 constexpr size_t contract_p_smem(int p) {
-  return (size_t)(p - 1) * padded_len(1 << LOGB) * sizeof(float2) + 64 * sizeof(float);
+  return (size_t)xoff<LOGB>(p) * sizeof(float2) + 64 * sizeof(float);
 }
-// Two resident blocks per SM where their shared memory fits (p <= 4 at b = 2^12), else one.
+// Two resident blocks per SM where their shared memory fits (p <= 5 at b = 2^12), else one.
 template <int LOGB, int P>
 constexpr int contract_p_min_blocks() {
   return 2 * (contract_p_smem<LOGB>(P) + 3 * 1024) <= 227 * 1024 ? 2 : 1;
 }
 
-// The P-1 transforms of one direction, interleaved two at a time (block_fft_pair).
+// The P-1 transforms of one direction: each odd k (length b) interleaved with the even k + 1
+// (length b/2) by block_fft_pair; a last odd k alone.
 template <int LOGB, int NT, int P, int DIR>
 __device__ __forceinline__ void power_sum_ffts(float2* X, const float2* tw) {
-  constexpr int stride = padded_len(1 << LOGB);
-#pragma unroll 1
-  for (int k = 0; k + 1 < P - 1; k += 2) block_fft_pair<LOGB, LOGB, NT, DIR>(X + k * stride, X + (k + 1) * stride, tw);
-  if constexpr ((P - 1) % 2 == 1) block_fft<LOGB, NT, DIR>(X + (P - 2) * stride, tw);
+#pragma unroll
+  for (int k = 1; k + 1 < P; k += 2)
+    block_fft_pair<LOGB, LOGB - 1, NT, DIR>(X + xoff<LOGB>(k), X + xoff<LOGB>(k + 1), tw);
+  if constexpr ((P - 1) % 2 == 1) block_fft<LOGB, NT, DIR>(X + xoff<LOGB>(P - 1), tw);
 }
 
 // Grid (B, L): block (m, tau) computes T^(m)(I,u_tau,...,u_tau) into Vall[tau][m] and
@@ -301,8 +319,9 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB), (contract_p_min_blocks
   constexpr int NT = threads_for_logb(LOGB);
   constexpr int m_roots = P < 4 ? 4 : 8;
   constexpr float inv_b = 1.f / (float)b;
+  constexpr int hb = b / 2;
   extern __shared__ float2 smem[];
-  float* red = reinterpret_cast<float*>(smem + (P - 1) * padded_len(b));
+  float* red = reinterpret_cast<float*>(smem + xoff<LOGB>(P));
   __shared__ float2 tw[kTwEntries];
   fill_twiddles(tw, NT);
   const int m = blockIdx.x, tau = blockIdx.y, n = a.n, tid = threadIdx.x;
@@ -327,8 +346,8 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB), (contract_p_min_blocks
       uscale = 1.f / sqrtf(ss);
     }
   }
-  // power-sum sketches s_k, k = 1..P-1, in X[k-1]
-  for (int i = tid; i < (P - 1) * padded_len(b); i += NT) smem[i] = make_float2(0.f, 0.f);
+  // power-sum sketches s_k, k = 1..P-1 (even k at half length)
+  for (int i = tid; i < xoff<LOGB>(P); i += NT) smem[i] = make_float2(0.f, 0.f);
   __syncthreads();
   for (int i = tid; i < n; i += NT) {
     const float x = __ldcg(u + i) * uscale;
@@ -338,7 +357,8 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB), (contract_p_min_blocks
     for (int k = 1; k < P; ++k) {
       xk *= x;
       const float2 v = cscale(root_of_unity(k * gi, m_roots), xk);
-      float* slot = reinterpret_cast<float*>(&smem[(k - 1) * padded_len(b) + pad_idx((k * hi) & (b - 1))]);
+      const int pos = (k & 1) ? (k * hi) & (b - 1) : ((k / 2) * hi) & (hb - 1);
+      float* slot = reinterpret_cast<float*>(&smem[xoff<LOGB>(k) + pad_idx(pos)]);
       atomicAdd(slot, v.x);
       atomicAdd(slot + 1, v.y);
     }
@@ -346,31 +366,47 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB), (contract_p_min_blocks
   __syncthreads();
   power_sum_ffts<LOGB, NT, P, -1>(smem, tw);
 
-  // per frequency: Y for the eigenvalue, then X_k <- FS conj(F R_k)
+  // per frequency pair (f, f + b/2): Y for the eigenvalue, then X_k <- FS conj(F R_k), the even
+  // k folded to length b/2
   float lam = 0.f;
-  for (int f = tid; f < b; f += NT) {
+  for (int f0 = tid; f0 < hb; f0 += NT) {
     float2 U[P];
     U[0] = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int k = 1; k < P; ++k) U[k] = smem[(k - 1) * padded_len(b) + pad_idx(f)];
-    float2 Y = make_float2(0.f, 0.f);
-    float2 R[P];
+    for (int k = 2; k < P; k += 2) U[k] = smem[xoff<LOGB>(k) + pad_idx(f0)];
+    float2 Wfold[P];
 #pragma unroll
-    for (int k = 0; k < P; ++k) R[k] = make_float2(0.f, 0.f);
-    constexpr CTerms<P> tt = TermTable<P>::value;
+    for (int k = 0; k < P; ++k) Wfold[k] = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int q = 0; q < tt.count; ++q) {
-      float2 prod = U[tt.parts[q][0]];
+    for (int half = 0; half < 2; ++half) {
+      const int f = f0 + half * hb;
 #pragma unroll
-      for (int j = 1; j < tt.nparts[q]; ++j) prod = cmul(prod, U[tt.parts[q][j]]);
-      prod = cscale(prod, tt.coef[q]);
-      if (tt.target[q] == 0) Y = cadd(Y, prod);
-      else R[tt.target[q]] = cadd(R[tt.target[q]], prod);
+      for (int k = 1; k < P; k += 2) U[k] = smem[xoff<LOGB>(k) + pad_idx(f)];
+      float2 Y = make_float2(0.f, 0.f);
+      float2 R[P];
+#pragma unroll
+      for (int k = 0; k < P; ++k) R[k] = make_float2(0.f, 0.f);
+      constexpr CTerms<P> tt = TermTable<P>::value;
+#pragma unroll
+      for (int q = 0; q < tt.count; ++q) {
+        float2 prod = U[tt.parts[q][0]];
+#pragma unroll
+        for (int j = 1; j < tt.nparts[q]; ++j) prod = cmul(prod, U[tt.parts[q][j]]);
+        prod = cscale(prod, tt.coef[q]);
+        if (tt.target[q] == 0) Y = cadd(Y, prod);
+        else R[tt.target[q]] = cadd(R[tt.target[q]], prod);
+      }
+      const float2 F = __ldcg(FSm + f);
+      lam += F.x * Y.x + F.y * Y.y;               // Re(F conj(Y))
+#pragma unroll
+      for (int k = 1; k < P; ++k) {
+        const float2 W = cmulconj(F, R[k]);
+        if (k & 1) smem[xoff<LOGB>(k) + pad_idx(f)] = W;
+        else Wfold[k] = cadd(Wfold[k], W);
+      }
     }
-    const float2 F = __ldcg(FSm + f);
-    lam += F.x * Y.x + F.y * Y.y;                 // Re(F conj(Y))
 #pragma unroll
-    for (int k = 1; k < P; ++k) smem[(k - 1) * padded_len(b) + pad_idx(f)] = cmulconj(F, R[k]);
+    for (int k = 2; k < P; k += 2) smem[xoff<LOGB>(k) + pad_idx(f0)] = Wfold[k];
   }
   lam *= inv_b;
   __syncthreads();
@@ -384,7 +420,8 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB), (contract_p_min_blocks
     float v = 0.f, xk = 1.f;                      // xk = x^(k-1)
 #pragma unroll
     for (int k = 1; k < P; ++k) {
-      const float2 G = smem[(k - 1) * padded_len(b) + pad_idx((k * hi) & (b - 1))];
+      const int pos = (k & 1) ? (k * hi) & (b - 1) : ((k / 2) * hi) & (hb - 1);
+      const float2 G = smem[xoff<LOGB>(k) + pad_idx(pos)];
       const float2 c = root_of_unity(-k * gi, m_roots);            // conj(sigma)^k
       v += (float)k * (c.x * G.x - c.y * G.y) * xk * inv_b;
       xk *= x;
@@ -411,7 +448,7 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB), (contract_p_min_blocks
   float* dst = a.Vmed ? a.Vmed + (size_t)tau * n : a.Unext + (size_t)tau * n;
   median_vector<NT>(a.Vall + (size_t)tau * a.B * n, a.B, n, dst,
                     a.Unext ? a.Unext + (size_t)tau * n : nullptr, red, a.status,
-                    reinterpret_cast<float*>(smem), 2 * (P - 1) * padded_len(b));
+                    reinterpret_cast<float*>(smem), 2 * xoff<LOGB>(P));
 }
 
 // Selection and deflation for order P: tau* = first argmax of lam_med, outputs, and per sketch m
