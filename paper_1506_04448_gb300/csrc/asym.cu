@@ -121,12 +121,13 @@ __global__ void __launch_bounds__(asym_threads<LOGB>(), 1) ivw_kernel(IvwArgs a)
     X[pad_idx(f)] = cmulconj(Xh[f], cmul(spec[f], X[pad_idx(f)]));
   if (threadIdx.x == 0) *last = cmulconj(Xh[N], cmul(spec[N], *last));
   __syncthreads();
-  block_irfft<LOGB, NT>(X, last, tw);
+  block_irfft<LOGB, NT, false>(X, last, tw);        // N z: the 1/N is applied at the read-off
   const int32_t* ho = hm + (size_t)a.o * a.nmax;
   const uint8_t* go = gm + (size_t)a.o * a.nmax;
   float* vout = a.Vall + ((size_t)r * a.B + m) * a.n_o;
+  constexpr float invN = 1.f / (float)N;
   for (int i = threadIdx.x; i < a.n_o; i += NT) {
-    const float v = real_at(X, ho[i] & (b - 1));
+    const float v = real_at(X, ho[i] & (b - 1)) * invN;
     vout[i] = (go[i] & 1) ? -v : v;
   }
   __threadfence();
@@ -347,10 +348,10 @@ __global__ void __launch_bounds__(asym_threads<LOGB>(), 1) cp_adjoint_kernel(CpA
     dl = block_sum<NT>(dl, red);
     if (threadIdx.x == 0) atomicAdd(&a.grad_lam[r], -2.f * dl / ((float)a.B * (float)b));
   }
-  block_irfft<LOGB, NT>(X, last, tw);
+  block_irfft<LOGB, NT, false>(X, last, tw);        // N z: the 1/N goes into `scale`
   const int32_t* hj = a.h + ((size_t)m * 3 + j) * a.nmax;
   const uint8_t* gj = a.g + ((size_t)m * 3 + j) * a.nmax;
-  const float scale = -2.f * a.lam[r] / (float)a.B;
+  const float scale = -2.f * a.lam[r] / ((float)a.B * (float)N);
   float* gr = a.grad[j] + (size_t)r * a.n[j];
   for (int i = threadIdx.x; i < a.n[j]; i += NT) {
     const float v = real_at(X, hj[i] & (b - 1));

@@ -326,7 +326,9 @@ __device__ __forceinline__ void block_rfft(float2* x, float2* last, const float2
 // Inverse: half spectrum -> z (the real signal, including the 1/b factor), in place.
 //   E_f = (X_f + conj X_{N-f})/2,  O_f = w^{-f} (X_f - conj X_{N-f})/2,  Z_f = E_f + i O_f,
 //   z = DFT_N^{-1}(Z) / N.
-template <int LOGB, int NT>
+// SCALE = false leaves out the final 1/N (one shared-memory pass) for callers that fold it into
+// what they do with z; the result is then N z.
+template <int LOGB, int NT, bool SCALE = true>
 __device__ __forceinline__ void block_irfft(float2* x, const float2* last, const float2* tw) {
   constexpr int N = 1 << (LOGB - 1);
   const float2 xN = *last;
@@ -350,9 +352,11 @@ __device__ __forceinline__ void block_irfft(float2* x, const float2* last, const
   }
   __syncthreads();
   block_fft<LOGB - 1, NT, +1>(x, tw);
-  constexpr float invN = 1.f / (float)N;
-  for (int t = threadIdx.x; t < N; t += NT) x[pad_idx(t)] = cscale(x[pad_idx(t)], invN);
-  __syncthreads();
+  if constexpr (SCALE) {
+    constexpr float invN = 1.f / (float)N;
+    for (int t = threadIdx.x; t < N; t += NT) x[pad_idx(t)] = cscale(x[pad_idx(t)], invN);
+    __syncthreads();
+  }
 }
 
 // Real element k of a signal held as complex pairs in the padded layout.
