@@ -65,7 +65,7 @@ def test_order3_hashes_are_the_colliding_hashes():
     np.testing.assert_array_equal(g, g3[:, 0])
 
 
-@pytest.mark.parametrize("p,n", [(3, 5), (4, 4), (4, 5), (5, 4)])
+@pytest.mark.parametrize("p,n", [(3, 5), (4, 4), (4, 5), (5, 4), (6, 3)])
 def test_collision_free_hashes_make_the_estimators_exact(p, n):
     T = random_symmetric_p(n, p, 100 + p)
     h, g, b = collision_free(n, p, 200 + p)
@@ -124,10 +124,11 @@ def test_fourth_roots_alias_at_order_four_and_eighth_roots_do_not():
     assert P.exact_uuu_p(T, u) == 0.0
 
 
-def test_order4_estimate_unbiased_over_hash_draws():
-    """Lemma 1's unbiasedness at p = 4: the mean of T^(u,u,u,u) over independent hash draws
-    matches T(u,u,u,u) within 4 standard errors."""
-    p, n, log2b, draws = 4, 6, 5, 600
+@pytest.mark.parametrize("p,n,draws", [(4, 6, 600), (5, 4, 400)])
+def test_order_p_estimate_unbiased_over_hash_draws(p, n, draws):
+    """Lemma 1's unbiasedness at p = 4 and 5: the mean of T^(u,...,u) over independent hash
+    draws matches T(u,...,u) within 4 standard errors."""
+    log2b = 5
     T = random_symmetric_p(n, p, 55)
     u = synth.rng(56).standard_normal(n)
     u /= np.linalg.norm(u)
