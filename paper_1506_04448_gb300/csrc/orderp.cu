@@ -27,88 +27,12 @@
 #include <stdio.h>
 
 #include "contract.cuh"
+#include "partitions.h"
 
 namespace tsk {
 
-constexpr int kMaxOrder = 6;
-constexpr int kMaxTerms = 48;
 // dynamic shared memory of sketch_p_kernel: the b <= 2^14 histogram and two n <= 8192 tables
 constexpr size_t kSketchPSmemMax = ((size_t)1 << 14) * sizeof(float2) + 2 * (size_t)8192 * sizeof(int);
-
-// The estimators' term table for order P, built at compile time (the kernel unrolls it, so every
-// product is a chain of complex multiplications on fixed registers): for each partition lambda of
-// P other than (P), a term 1/z_lambda of Y over all of lambda's parts; for each part size k < P
-// in lambda, a term m_k(lambda)/z_lambda of F R_k over lambda's other parts.  Partitions of P are
-// enumerated in reverse lexicographic order (the classic successor rule: strip trailing ones,
-// decrement the last part above one, refill with copies of it and the remainder).
-template <int P>
-struct CTerms {
-  float coef[kMaxTerms];
-  int target[kMaxTerms];
-  int nparts[kMaxTerms];
-  int parts[kMaxTerms][kMaxOrder];
-  int count;
-};
-
-template <int P>
-constexpr CTerms<P> compile_terms() {
-  CTerms<P> out{};
-  out.count = 0;
-  int a[kMaxOrder + 1] = {};
-  int len = 1;
-  a[0] = P;
-  while (true) {
-    // z_lambda = prod_k k^{m_k} m_k! for the partition a[0..len)
-    int mult[kMaxOrder + 1] = {};
-    for (int j = 0; j < len; ++j) ++mult[a[j]];
-    long long z = 1;
-    for (int k = 1; k <= P; ++k)
-      for (int j = 1; j <= mult[k]; ++j) z *= (long long)k * j;
-    if (!(len == 1 && a[0] == P)) {
-      out.coef[out.count] = 1.0f / (float)z;
-      out.target[out.count] = 0;
-      out.nparts[out.count] = len;
-      for (int j = 0; j < len; ++j) out.parts[out.count][j] = a[j];
-      ++out.count;
-    }
-    for (int k = 1; k < P; ++k) {
-      if (mult[k] == 0) continue;
-      out.coef[out.count] = (float)mult[k] / (float)z;
-      out.target[out.count] = k;
-      int c = 0;
-      bool dropped = false;
-      for (int j = 0; j < len; ++j) {
-        if (!dropped && a[j] == k) {
-          dropped = true;
-          continue;
-        }
-        out.parts[out.count][c++] = a[j];
-      }
-      out.nparts[out.count] = c;
-      ++out.count;
-    }
-    int rem = 0;
-    while (len > 0 && a[len - 1] == 1) {
-      ++rem;
-      --len;
-    }
-    if (len == 0) break;
-    a[len - 1] -= 1;
-    ++rem;
-    const int x = a[len - 1];
-    while (rem > x) {
-      a[len++] = x;
-      rem -= x;
-    }
-    a[len++] = rem;
-  }
-  return out;
-}
-
-template <int P>
-struct TermTable {
-  static constexpr CTerms<P> value = compile_terms<P>();
-};
 
 // exp(2 pi i j / m) for m in {4, 8} (the sign roots), j taken mod m.
 __device__ __forceinline__ float2 root_of_unity(int j, int m) {
