@@ -202,7 +202,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": f"{per_step} of the L=50 vectors per step"},
+            "config": {"workload": WORKLOAD, "n": cfg["n"], "k": cfg["k"], "B": cfg["B"],
+                       "b": 1 << cfg["log2b"], "L": cfg["L"], "T": cfg["T"],
+                       "parallelism": "one host core",
+                       "sample": f"{per_step} of the L=50 vectors per step"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{per_step} T^(I,u,u) evaluations (B=10 sketches each, "
                                        "numpy FP64 FFT engine, random sketch values) per step",
