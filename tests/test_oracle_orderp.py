@@ -166,3 +166,19 @@ def test_sketched_order_p_rtpm_with_collision_free_hashes_is_the_plain_method(p,
     ref = P.rtpm_exact_p(T, U0, 8)
     np.testing.assert_allclose(res["lam"], ref["lam"], rtol=1e-8)
     np.testing.assert_allclose(res["V"], ref["V"], atol=1e-8)
+
+
+def test_order_p_hash_golden_fixture():
+    """Frozen order-p hash values (tests/golden/hashes_order_p_seed3.txt, written by
+    tests/golden/make_golden.py from the oracle alone): guards the degree-(2p-1) bucket
+    polynomial and the mod-8 sign index against drift."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "hashes_order_p_seed3.txt")
+    rows = [line.split() for line in open(path) if not line.startswith("#")]
+    assert len(rows) == 2 * 2 * 6
+    for p in (4, 6):
+        h, g = P.cs_hashes_p(3, 2, 12, p, 6)
+        for ps, ms, i_s, hv, gv in rows:
+            if int(ps) == p:
+                assert h[int(ms), int(i_s)] == int(hv) and g[int(ms), int(i_s)] == int(gv)
+    assert all(0 <= int(r[4]) < 8 for r in rows)
