@@ -9,6 +9,8 @@
 // the other B-1 sketches.  For the colliding sketch only the wedge i <= j <= k is read, each
 // entry weighted by kappa in {1, 3, 6} (Sec. 3.3); each entry lands in exactly one component
 // because sigma_i sigma_j sigma_k = sqrt(-1)^((g_i + g_j + g_k) mod 4).
+#include <type_traits>
+
 #include "common.cuh"
 #include "fft.cuh"
 
@@ -149,6 +151,381 @@ __global__ void __launch_bounds__(1024, 1) sketch_sym_kernel(SymSketchArgs a) {
   }
 }
 
+// ------------------------------------------------------------------ colliding build, exact int32
+//
+// The FP32 colliding build of Eq. 7 in integer fixed point.  Shared-memory FP32 atomics run as a
+// compare-and-swap loop on this part (about 9 SM cycles per random warp-wide add, measured);
+// 32-bit integer adds are native (about 2.7 cycles, 4.7 with the returned old value).  So every
+// entry is quantised once, q = rint(kappa x 2^(25-E)) with 2^E > max|T| over the wedge (a
+// prepass), and the buckets are accumulated as wrapping int32 sums.  The returned old value
+// tells the warp when an add may have wrapped past +-2^31; the exact check then adds the carry
+// +-1 to a global int32 array, so every bucket's integer total is exact.  Block partials are
+// written to a workspace and summed in int64 by a separate kernel, which scales by 2^(E-25)
+// once.  The result is deterministic; its only roundings are the quantisation of each entry
+// (at most 2^(E-26), below 6e-8 of max|T|) and the final conversion to float.
+
+// rows before wedge row i: sum_{i' < i} (n - i') = i n - i (i - 1) / 2
+__device__ __forceinline__ long long wedge_rows_before(long long n, long long i) {
+  return i * n - i * (i - 1) / 2;
+}
+
+// |x| rounded up to float, as raw bits (ordered like the values for non-negative floats; NaN
+// and infinity compare above every finite value)
+__device__ __forceinline__ uint32_t absbits(float x) { return __float_as_uint(fabsf(x)); }
+__device__ __forceinline__ uint32_t absbits(double x) {
+  return __float_as_uint(__double2float_ru(fabs(x)));
+}
+__device__ __forceinline__ uint32_t absbits(int32_t x) {
+  return __float_as_uint(__ll2float_ru(llabs((long long)x)));
+}
+
+constexpr int kMaxTileCols = 256;   // nc = ceil(n / 32) for n <= 8192
+
+// Wedge tiles.  The wedge {i <= j <= k < n} is covered by tiles (rb, c, i): plane i, rows j in
+// [32 rb, 32 rb + 32) with j >= i, columns k in [32 c, 32 c + 32) with k >= j, for
+// rb <= c < nc = ceil(n / 32) and i < min(32 rb + 32, n).  One warp takes one tile: lane l owns
+// column k = 32 c + l (one coalesced 128-byte row segment per row), so the column's hash words
+// stay in registers while the warp walks the tile's rows.  Within a row block rb the tiles are
+// numbered column-major over the planes that reach it.
+
+// max |T_ijk| over the wedge i <= j <= k as float bits, into *maxbits (zeroed by the caller).
+// Warps take the wedge's tiles (all planes) and load a tile's up to 32 rows at once.
+template <typename TIn>
+__global__ void __launch_bounds__(256) wedge_absmax_kernel(const TIn* __restrict__ T, int n,
+                                                           unsigned* maxbits) {
+  __shared__ unsigned smax;
+  __shared__ int pre[kMaxTileCols + 1];   // tiles before row block rb
+  const int nc = (n + 31) >> 5;
+  if (threadIdx.x == 0) {
+    smax = 0u;
+    int acc = 0;
+    for (int rb = 0; rb < nc; ++rb) {
+      pre[rb] = acc;
+      acc += min(n, 32 * rb + 32) * (nc - rb);
+    }
+    pre[nc] = acc;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  uint32_t mb = 0u;
+  for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < pre[nc]; it += nwarps) {
+    int lo = 0, hi = nc - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (pre[mid] <= it) lo = mid; else hi = mid - 1;
+    }
+    const int rb = lo;
+    const int nir = min(n, 32 * rb + 32);
+    const int local = it - pre[rb];
+    const int c = rb + local / nir;
+    const int i = local % nir;
+    const int jlo = max(i, 32 * rb), jhi = min(32 * rb + 32, n);
+    const int k = 32 * c + lane;
+    const int jlim = k >= n ? -1 : (rb == c ? min(k, jhi - 1) : jhi - 1);
+    const TIn* col = T + ((size_t)i * n + jlo) * n + (k < n ? k : n - 1);
+    TIn x[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      x[r] = (TIn)0;
+      if (jlo + r <= jlim) x[r] = __ldcg(col + (size_t)r * n);
+    }
+#pragma unroll
+    for (int r = 0; r < 32; ++r) mb = max(mb, absbits(x[r]));
+  }
+  mb = __reduce_max_sync(0xffffffffu, mb);
+  if (lane == 0) atomicMax(&smax, mb);
+  __syncthreads();
+  if (threadIdx.x == 0 && smax != 0u) atomicMax(maxbits, smax);
+}
+
+// Quantisation for max|T| bits `mb`: q = rint(kappa x 2^(25-E)) with 2^E > max|T|, so
+// |q| < 6 2^25 < 2^28.  The factor 2^(25-E) is applied as sa (and sb, only when it is not a
+// normal float by itself).
+constexpr int kFixBits = 25;
+
+struct FixScale {
+  float sa, sb;
+  int e;        // E
+  bool finite;
+};
+__device__ __forceinline__ FixScale fix_scale(uint32_t mb) {
+  FixScale f;
+  f.finite = mb < 0x7f800000u;
+  int e = 0;
+  if (mb != 0u && f.finite) frexpf(__uint_as_float(mb), &e);   // max|T| < 2^e
+  const int k = kFixBits - e;                                  // k in [-103, 174]
+  const bool one = k >= -120 && k <= 120;
+  f.sa = ldexpf(1.f, one ? k : k / 2);
+  f.sb = one ? 1.f : ldexpf(1.f, k - k / 2);
+  f.e = e;
+  return f;
+}
+
+constexpr int kMaxFixSlabs = 256;
+
+struct SymFixArgs {
+  const void* T;
+  int n;
+  const int32_t* h;     // [B][n]
+  const uint8_t* g;     // [B][n]
+  int B;
+  int log2b;
+  int log2r;            // 2^log2r bucket ranges, one block each
+  int nslab;
+  const unsigned* maxbits;
+  int* carry;           // [B][2b]: wraps of the int32 sums past +-2^31
+  int* part;            // [nslab][B][2b]: per-block integer partials
+  int plane0[kMaxFixSlabs + 1];   // slab s holds the planes [plane0[s], plane0[s + 1])
+};
+
+// Packed hash word of index i for the fixed-point build: 8 h(i) + g(i) 2^30 (mod 2^32).  In the
+// sum sq of the words of i, j, k, bits 3..20 carry 8 (h_i + h_j + h_k) < 2^21 and bits 30..31
+// carry (g_i + g_j + g_k) mod 4, the exponent of sigma_i sigma_j sigma_k = sqrt(-1)^e: bit 31 is
+// its sign and bit 30 picks the imaginary part.  So the byte offset 8 t + 4 (e & 1) of the
+// bucket's re/im cell is (sq & 8 mask) | ((sq >> 28) & ~(8 mask)), and the sign is sq's top bit.
+__device__ __forceinline__ uint32_t fix_word(int32_t h, uint8_t g, int mask) {
+  return ((uint32_t)(h & mask) << 3) + ((uint32_t)(g & 3) << 30);
+}
+
+// One batch of 8 rows j0..j0+7 of a tile for every sketch of the block: y[r] is row j0 + r's
+// entry already scaled by kappa 2^(25-E) (0 for a lane that has no entry there).  Each add goes
+// to a valid cell even when its value is 0, so no lane is masked off; the adds go out back to
+// back and their returned old values are checked for wraps afterwards.
+template <int SK, bool RANGES>
+__device__ __forceinline__ void sym_fix_batch(const SymFixArgs& a, int* hist, const uint32_t* qs,
+                                              const uint32_t* qik, const float* y, int j0,
+                                              int jhi, int m0, int rr) {
+  const int n = a.n;
+  const int b = 1 << a.log2b;
+  const int mask = b - 1;
+  const uint32_t m8 = 8u * (uint32_t)mask;
+  const int br = RANGES ? b >> a.log2r : b;
+  const int cells = 2 * br;
+  const int shift_r = a.log2b - a.log2r;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < SK; ++s) {
+    // lane r of the warp holds row j0 + r's word
+    const uint32_t qrow = qs[s * n + min(j0 + (lane & 7), jhi - 1)];
+    char* hb = reinterpret_cast<char*>(hist + s * cells);
+    int v[8], old[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const uint32_t sq = qik[s] + __shfl_sync(0xffffffffu, qrow, r);
+      uint32_t off;
+      v[r] = __float2int_rn(__uint_as_float(__float_as_uint(y[r]) ^ (sq & 0x80000000u)));
+      if (RANGES) {
+        const int t = (int)(sq >> 3) & mask;
+        if ((t >> shift_r) != rr) v[r] = 0;
+        off = 8u * (uint32_t)(t & (br - 1)) + ((sq >> 28) & 4u);
+      } else {
+        off = (sq & m8) | ((sq >> 28) & ~m8);
+      }
+      old[r] = atomicAdd(reinterpret_cast<int*>(hb + off), v[r]);
+    }
+    // |v| < 2^28, so an add can wrap only if |old| >= 2^30, i.e. old + 2^30 has its top bit set
+    unsigned near = 0u;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) near |= (unsigned)old[r] + 0x40000000u;
+    // exact check, carry +-2^32 for each wrapped add (rare); entered by the whole warp, since the
+    // row words come back by shuffles over all lanes
+    if (__any_sync(0xffffffffu, (int)near < 0)) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int sum = (int)((unsigned)old[r] + (unsigned)v[r]);
+        const uint32_t sq = qik[s] + __shfl_sync(0xffffffffu, qrow, r);
+        if (((old[r] ^ sum) & (v[r] ^ sum)) < 0) {
+          const int t = (int)(sq >> 3) & mask;
+          atomicAdd(&a.carry[(size_t)(m0 + s) * 2 * b + 2 * t + (int)((sq >> 30) & 1)],
+                    v[r] > 0 ? 1 : -1);
+        }
+      }
+    }
+  }
+}
+
+// Interior tile (no row j == i, no diagonal element k == j, kappa = 6) of whole 8-row batches:
+// unconditional loads (a lane beyond the tensor reads column n - 1 and scales it by 0), the next
+// batch's loads issued before the current batch's adds.
+template <typename TIn, int SK, bool RANGES, bool TWO>
+__device__ __forceinline__ void sym_fix_rows_interior(const SymFixArgs& a, const FixScale& fs,
+                                                      int* hist, const uint32_t* qs,
+                                                      const TIn* col, bool kin, int jlo, int jhi,
+                                                      const uint32_t* qik, int m0, int rr) {
+  const int n = a.n;
+  const float ks = kin ? 6.f * fs.sa : 0.f;
+  TIn xa[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) xa[r] = __ldcg(col + (size_t)r * n);
+  for (int j0 = jlo; j0 < jhi; j0 += 8) {
+    TIn xb[8];
+    if (j0 + 8 < jhi) {
+      const TIn* p = col + (size_t)(j0 + 8 - jlo) * n;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) xb[r] = __ldcg(p + (size_t)r * n);
+    }
+    float y[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      y[r] = (float)xa[r] * ks;
+      if (TWO) y[r] *= fs.sb;
+    }
+    sym_fix_batch<SK, RANGES>(a, hist, qs, qik, y, j0, jhi, m0, rr);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) xa[r] = xb[r];
+  }
+}
+
+// Any tile: rows [jlo, jhi) 8 at a time, loads only where the lane has an entry (j <= jlim).
+template <typename TIn, int SK, bool RANGES, bool TWO>
+__device__ __forceinline__ void sym_fix_rows_edge(const SymFixArgs& a, const FixScale& fs,
+                                                  int* hist, const uint32_t* qs, const TIn* col,
+                                                  int i, int k, int jlo, int jhi, int jlim,
+                                                  const uint32_t* qik, int m0, int rr) {
+  const int n = a.n;
+  const float ks1 = fs.sa, ks3 = 3.f * fs.sa, ks6 = 6.f * fs.sa;
+  for (int j0 = jlo; j0 < jhi; j0 += 8) {
+    const TIn* p = col + (size_t)(j0 - jlo) * n;
+    float y[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int j = j0 + r;
+      TIn x = (TIn)0;
+      if (j <= jlim) x = __ldcg(p + (size_t)r * n);
+      // kappa = number of orderings of (i, j, k): 6 when all differ, 3 when two agree
+      const float ks = (j == i) ? (k == j ? ks1 : ks3) : (k == j ? ks3 : ks6);
+      y[r] = (float)x * ks;
+      if (TWO) y[r] *= fs.sb;
+    }
+    sym_fix_batch<SK, RANGES>(a, hist, qs, qik, y, j0, jhi, m0, rr);
+  }
+}
+
+// The tiles of one block: planes [i0, i1), row blocks rb >= rb0 = i0 / 32, columns c >= rb,
+// planes i < 32 rb + 32 only.  For row block rb there are (min(i1, 32 rb + 32) - i0) planes
+// times (nc - rb) columns; pre[] holds the running counts.
+template <typename TIn, int SK, bool RANGES, bool TWO>
+__device__ __forceinline__ void sym_fix_tiles(const SymFixArgs& a, const FixScale& fs, int* hist,
+                                              const uint32_t* qs, const int* pre, int nrb,
+                                              int* next, int i0, int i1, int m0, int rr) {
+  const int n = a.n;
+  const int rb0 = i0 >> 5;
+  const int lane = threadIdx.x & 31;
+  const TIn* T = static_cast<const TIn*>(a.T);
+  const int items = pre[nrb];
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(next, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= items) break;
+    int lo = 0, hi = nrb - 1;   // row block: last with pre[.] <= it
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (pre[mid] <= it) lo = mid; else hi = mid - 1;
+    }
+    const int rb = rb0 + lo;
+    const int nir = min(i1, 32 * rb + 32) - i0;
+    const int local = it - pre[lo];
+    const int c = rb + local / nir;
+    const int i = i0 + local % nir;
+    const int jlo = max(i, 32 * rb), jhi = min(32 * rb + 32, n);
+    const int k = 32 * c + lane;
+    // last row this lane takes part in: the tile's last row, k itself on the diagonal block
+    // (j <= k), none beyond the tensor
+    const int jlim = k >= n ? -1 : (rb == c ? min(k, jhi - 1) : jhi - 1);
+    // a lane beyond the tensor adds zeros; it takes the word of k mod n, so that its cells are
+    // spread like everyone else's (one shared cell would serialise those adds)
+    uint32_t qik[SK];
+#pragma unroll
+    for (int s = 0; s < SK; ++s) qik[s] = qs[s * n + i] + qs[s * n + (k < n ? k : k % n)];
+    const TIn* col = T + ((size_t)i * n + jlo) * n + (k < n ? k : n - 1);
+    if (jlo > i && rb < c && ((jhi - jlo) & 7) == 0)
+      sym_fix_rows_interior<TIn, SK, RANGES, TWO>(a, fs, hist, qs, col, k < n, jlo, jhi, qik, m0, rr);
+    else
+      sym_fix_rows_edge<TIn, SK, RANGES, TWO>(a, fs, hist, qs, col, i, k, jlo, jhi, jlim, qik, m0, rr);
+  }
+}
+
+// Block (group of SK sketches, bucket range rr, slab of planes).  The block's warps take its
+// wedge tiles from a shared counter; per batch of 8 rows a warp has 8 loads in flight per lane,
+// scales each entry by kappa 2^(25-E) and, per sketch, flips its sign, rounds it to int32 and
+// adds it to the bucket's re or im cell.
+template <typename TIn, int SK, bool RANGES>
+__global__ void __launch_bounds__(1024, 1) sketch_sym_fix_kernel(SymFixArgs a) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __shared__ int s_next;
+  __shared__ int s_pre[kMaxTileCols + 1];
+  const FixScale fs = fix_scale(*a.maxbits);
+  if (!fs.finite) return;   // the reduce kernel writes NaN
+  const int b = 1 << a.log2b;
+  const int n = a.n;
+  const int mask = b - 1;
+  const int R = RANGES ? 1 << a.log2r : 1;
+  const int br = RANGES ? b >> a.log2r : b;
+  const int cells = 2 * br;   // re/im interleaved, like the output
+  int* hist = reinterpret_cast<int*>(sm_raw);                                  // [SK][cells]
+  uint32_t* qs = reinterpret_cast<uint32_t*>(sm_raw + (size_t)SK * cells * sizeof(int));  // [SK][n]
+  const int grp = blockIdx.x / R;
+  const int rr = blockIdx.x % R;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int m0 = grp * SK;
+  const int i0 = a.plane0[blockIdx.y], i1 = a.plane0[blockIdx.y + 1];
+  const int nc = (n + 31) >> 5;
+  const int rb0 = i0 >> 5;
+  const int nrb = nc - rb0;
+  for (int i = tid; i < SK * cells; i += nt) hist[i] = 0;
+  for (int s = 0; s < SK; ++s) {
+    const int m = m0 + s;
+    for (int i = tid; i < n; i += nt) qs[s * n + i] = fix_word(a.h[(size_t)m * n + i], a.g[(size_t)m * n + i], mask);
+  }
+  if (tid == 0) {
+    s_next = 0;
+    int acc = 0;
+    for (int q = 0; q < nrb; ++q) {
+      s_pre[q] = acc;
+      const int rb = rb0 + q;
+      acc += (min(i1, 32 * rb + 32) - i0) * (nc - rb);
+    }
+    s_pre[nrb] = acc;
+  }
+  __syncthreads();
+  if (fs.sb == 1.f)
+    sym_fix_tiles<TIn, SK, RANGES, false>(a, fs, hist, qs, s_pre, nrb, &s_next, i0, i1, m0, rr);
+  else
+    sym_fix_tiles<TIn, SK, RANGES, true>(a, fs, hist, qs, s_pre, nrb, &s_next, i0, i1, m0, rr);
+  __syncthreads();
+  for (int s = 0; s < SK; ++s) {
+    int* dst = a.part + ((size_t)blockIdx.y * a.B + (m0 + s)) * 2 * b + (size_t)2 * rr * br;
+    for (int c = tid; c < cells; c += nt) dst[c] = hist[s * cells + c];
+  }
+}
+
+// S[m][c] (+)= 2^(E-25) (sum over slabs of part[.][m][c] + 2^32 carry[m][c]); NaN if max|T| is
+// not finite (also reported as TSK_ENONFINITE).
+__global__ void __launch_bounds__(256) sym_fix_reduce_kernel(const int* __restrict__ part,
+                                                             const int* __restrict__ carry,
+                                                             const unsigned* maxbits, int nslab,
+                                                             long long cells, float* S,
+                                                             int accumulate, int* status) {
+  const FixScale fs = fix_scale(*maxbits);
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < cells;
+       c += (long long)gridDim.x * blockDim.x) {
+    float v;
+    if (fs.finite) {
+      long long acc = (long long)carry[c] * 4294967296LL;
+#pragma unroll 8
+      for (int s = 0; s < nslab; ++s) acc += __ldcg(part + (size_t)s * cells + c);
+      // one rounding (int64 -> float), then an exact power-of-two scaling
+      v = ldexpf(__ll2float_rn(acc), fs.e - kFixBits);
+    } else {
+      v = __int_as_float(0x7fc00000);
+      if (c == 0) tsk_set_status(status, TSK_ENONFINITE);
+    }
+    S[c] = accumulate ? S[c] + v : v;
+  }
+}
+
 struct AsymSketchArgs {
   const void* T;
   int n1, n2, n3, nmax;
@@ -246,6 +623,114 @@ static int launch_sym(const SymSketchArgs& a0, int B, tsk_ctx* ctx) {
   a.nslab = (int)nslab;
   dim3 grid(B * PARTS * R, (unsigned)nslab);
   kernel<<<grid, 1024, smem, ctx->stream>>>(a);
+  TSK_CHECK_LAUNCH();
+  return TSK_OK;
+}
+
+template <typename TIn, int SK, bool RANGES>
+static int launch_sym_fix_t(const SymFixArgs& a, int groups, size_t smem, tsk_ctx* ctx) {
+  auto kernel = sketch_sym_fix_kernel<TIn, SK, RANGES>;
+  TSK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(groups << a.log2r, (unsigned)a.nslab);
+  kernel<<<grid, 1024, smem, ctx->stream>>>(a);
+  TSK_CHECK_LAUNCH();
+  return TSK_OK;
+}
+
+template <typename TIn>
+static int launch_sym_fix(const void* T, int n, const int32_t* h, const uint8_t* g, int B,
+                          int log2b, void* S, int accumulate, tsk_ctx* ctx) {
+  const size_t b = (size_t)1 << log2b;
+  const size_t smax = (size_t)ctx->max_smem_optin - 2048;   // the kernel's static tables
+  auto smem_for = [&](int sk, int lr) {
+    return (size_t)sk * 2 * (b >> lr) * sizeof(int) + (size_t)sk * n * sizeof(uint32_t) + 16;
+  };
+  // fewest bucket ranges whose histogram fits; then the most sketches per block (dividing B,
+  // so every block of a slab does the same work) that still fit
+  int log2r = 0;
+  while (smem_for(1, log2r) > smax && log2r < 4) ++log2r;
+  if (smem_for(1, log2r) > smax) return TSK_EUNSUPPORTED;
+  int SK = 1;
+  if (std::is_same<TIn, float>::value && log2r == 0) {
+    if (B % 4 == 0 && smem_for(4, 0) <= smax) SK = 4;
+    else if (B % 2 == 0 && smem_for(2, 0) <= smax) SK = 2;
+  }
+  const size_t smem = smem_for(SK, log2r);
+  const int groups = B / SK;
+  const int R = 1 << log2r;
+  SymFixArgs a{};
+  a.T = T;
+  a.n = n;
+  a.h = h;
+  a.g = g;
+  a.B = B;
+  a.log2b = log2b;
+  a.log2r = log2r;
+  // one wave of 1024-thread blocks (one per SM); slabs are plane ranges of about equal wedge
+  // size (plane i holds (n - i)(n - i + 1) / 2 entries), none below ~16k entries
+  const long long W = (long long)n * (n + 1) * (n + 2) / 6;
+  long long nslab = (long long)ctx->num_sms / ((long long)groups * R);
+  if (nslab < 1) nslab = 1;
+  const long long cap = (W + 16383) / 16384;
+  if (nslab > cap) nslab = cap;
+  if (nslab > n) nslab = n;
+  if (nslab > kMaxFixSlabs) nslab = kMaxFixSlabs;
+  a.nslab = (int)nslab;
+  {
+    // slabs of about equal cost: plane i costs its tiles' row batches (rows rounded up to 8)
+    // times their columns, over the row blocks rb >= i / 32 it reaches
+    const int nc = (n + 31) / 32;
+    auto plane_cost = [n, nc](int i) {
+      long long cost = 0;
+      for (int rb = i / 32; rb < nc; ++rb) {
+        const int rows = (rb * 32 + 32 < n ? rb * 32 + 32 : n) - (i > 32 * rb ? i : 32 * rb);
+        cost += (long long)((rows + 7) / 8) * (nc - rb);
+      }
+      return cost;
+    };
+    long long total = 0;
+    for (int i = 0; i < n; ++i) total += plane_cost(i);
+    a.plane0[0] = 0;
+    int i = 0, s = 1;
+    long long acc = 0;
+    while (s < a.nslab && i < n) {
+      acc += plane_cost(i++);
+      while (s < a.nslab && acc * a.nslab >= total * s) a.plane0[s++] = i;
+    }
+    while (s < a.nslab) a.plane0[s++] = n;
+    a.plane0[a.nslab] = n;
+    for (int q = 1; q < a.nslab; ++q)   // keep every slab non-empty (nslab <= n)
+      if (a.plane0[q] <= a.plane0[q - 1]) a.plane0[q] = a.plane0[q - 1] + 1;
+    for (int q = a.nslab - 1; q >= 1; --q)
+      if (a.plane0[q] >= a.plane0[q + 1]) a.plane0[q] = a.plane0[q + 1] - 1;
+  }
+  const size_t cells = (size_t)B * 2 * b;
+  const size_t head = ws_round(256) + ws_round(cells * sizeof(int));
+  int rc = tsk_ws_reserve(ctx, head + ws_round((size_t)a.nslab * cells * sizeof(int)));
+  if (rc != TSK_OK) return rc;
+  WsCarve wc{static_cast<char*>(ctx->ws), 0};
+  unsigned* maxbits = wc.take<unsigned>(64);
+  a.carry = wc.take<int>(cells);
+  a.part = wc.take<int>((size_t)a.nslab * cells);
+  a.maxbits = maxbits;
+  TSK_CUDA(cudaMemsetAsync(ctx->ws, 0, head, ctx->stream));
+  wedge_absmax_kernel<TIn><<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(static_cast<const TIn*>(T), n,
+                                                                    maxbits);
+  TSK_CHECK_LAUNCH();
+  if constexpr (std::is_same<TIn, float>::value) {
+    if (SK == 4) rc = launch_sym_fix_t<TIn, 4, false>(a, groups, smem, ctx);
+    else if (SK == 2) rc = launch_sym_fix_t<TIn, 2, false>(a, groups, smem, ctx);
+  }
+  if (SK == 1) {
+    if (log2r == 0) rc = launch_sym_fix_t<TIn, 1, false>(a, groups, smem, ctx);
+    else rc = launch_sym_fix_t<TIn, 1, true>(a, groups, smem, ctx);
+  }
+  if (rc != TSK_OK) return rc;
+  long long blocks = ((long long)cells + 255) / 256;
+  if (blocks > (long long)ctx->num_sms * 8) blocks = (long long)ctx->num_sms * 8;
+  sym_fix_reduce_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(
+      a.part, a.carry, maxbits, a.nslab, (long long)cells, static_cast<float*>(S), accumulate,
+      ctx->status);
   TSK_CHECK_LAUNCH();
   return TSK_OK;
 }
@@ -445,17 +930,20 @@ extern "C" int sketch_tensor(tsk_ctx* ctx, const void* T, int in_dtype, int M,
     if (dims_host[j] < 0 || dims_host[j] > 8192) return dims_host[j] < 0 ? TSK_EINVAL : TSK_EUNSUPPORTED;
   const size_t b = (size_t)1 << log2b;
   const size_t elem = acc_dtype == TSK_C64 ? sizeof(float) : 8;
+  if (M == 1 && acc_dtype == TSK_C64 && dims_host[0] > 0) {
+    // complex-float colliding sketches: exact int32 accumulation (writes or adds S itself)
+    const int n = (int)dims_host[0];
+    if (log2b > 16) return TSK_EUNSUPPORTED;
+    if (in_dtype == TSK_F32) return launch_sym_fix<float>(T, n, h, g, B, log2b, S, accumulate, ctx);
+    if (in_dtype == TSK_F64) return launch_sym_fix<double>(T, n, h, g, B, log2b, S, accumulate, ctx);
+    return launch_sym_fix<int32_t>(T, n, h, g, B, log2b, S, accumulate, ctx);
+  }
   if (!accumulate) TSK_CUDA(cudaMemsetAsync(S, 0, (size_t)B * b * 2 * elem, ctx->stream));
   if (M == 1) {
     const int n = (int)dims_host[0];
     if (n == 0) return TSK_OK;
     if (log2b > 16) return TSK_EUNSUPPORTED;
     SymSketchArgs a{T, n, h, g, log2b, (long long)n * (n + 1) * (n + 2) / 6, 1, S, 0};
-    if (acc_dtype == TSK_C64) {
-      if (in_dtype == TSK_F32) return launch_sym<float, float, 1>(a, B, ctx);
-      if (in_dtype == TSK_F64) return launch_sym<double, float, 1>(a, B, ctx);
-      return launch_sym<int32_t, float, 1>(a, B, ctx);
-    }
     if (acc_dtype == TSK_C128) {
       if (in_dtype == TSK_F32) return launch_sym<float, double, 2>(a, B, ctx);
       return launch_sym<double, double, 2>(a, B, ctx);

@@ -86,6 +86,68 @@ def test_sketch_accumulate_is_linear(dev):
     assert rel(S.cpu().numpy(), R.cpu().numpy()) < 1e-5
 
 
+@pytest.mark.parametrize("n,log2b,B", [(64, 8, 2), (48, 9, 4), (40, 15, 2)])
+def test_symmetric_sketch_exact_through_int32_wraps(dev, n, log2b, B):
+    """The all-ones tensor quantises every wedge entry to 2^26, so most buckets' int32 sums wrap
+    past 2^31 many times: the result is right only if every carry is counted.  Its sketch has
+    integer entries below 2^24 (sums of kappa-weighted sigma products), exact in float."""
+    b = 1 << log2b
+    T = np.ones((n, n, n))
+    h, g = tsk.cs_hashes(7 + n, B, log2b, [n], dev)
+    ho, go = O.cs_hashes(7 + n, B, log2b, [n])
+    S = tsk.sketch_tensor(t32(T, dev), h, g, log2b).cpu().numpy()
+    for m in range(B):
+        np.testing.assert_array_equal(S[m], O.sketch_tensor_sym(T, ho[m, 0], go[m, 0], b))
+
+
+@pytest.mark.parametrize("scale", [1e-30, 1e-3, 1e6, 1e30])
+def test_symmetric_sketch_any_magnitude(dev, scale):
+    """The fixed-point step follows max|T| (a power of two), so tiny and huge tensors keep the
+    same relative accuracy; two builds of the same tensor are bit-identical."""
+    n, log2b, B = 23, 10, 4
+    b = 1 << log2b
+    T = synth.random_symmetric(n, 31) * scale
+    T[3, 5, 7] = T[3, 7, 5] = T[5, 3, 7] = T[5, 7, 3] = T[7, 3, 5] = T[7, 5, 3] = 40 * scale
+    h, g = tsk.cs_hashes(9, B, log2b, [n], dev)
+    ho, go = O.cs_hashes(9, B, log2b, [n])
+    Td = t32(T, dev)
+    S = tsk.sketch_tensor(Td, h, g, log2b).cpu().numpy()
+    S2 = tsk.sketch_tensor(Td, h, g, log2b).cpu().numpy()
+    np.testing.assert_array_equal(S, S2)
+    T32 = T.astype(np.float32).astype(np.float64)
+    for m in range(B):
+        assert rel(S[m], O.sketch_tensor_sym(T32, ho[m, 0], go[m, 0], b)) < 1e-5
+
+
+def test_symmetric_sketch_of_zero_and_nonfinite_tensors(dev):
+    n, log2b, B = 9, 8, 2
+    h, g = tsk.cs_hashes(4, B, log2b, [n], dev)
+    Z = torch.zeros((n, n, n), dtype=torch.float32, device=dev)
+    assert not tsk.sketch_tensor(Z, h, g, log2b).cpu().numpy().any()
+    tsk.check_status(dev)
+    Z[1, 2, 3] = float("nan")
+    S = tsk.sketch_tensor(Z, h, g, log2b).cpu().numpy()
+    assert np.isnan(S.real).all()
+    assert tsk.ctx_status(dev) == -5     # TSK_ENONFINITE
+    tsk.check_status(dev)
+
+
+@pytest.mark.parametrize("n,log2b,B", [(50, 12, 4), (33, 13, 6), (61, 12, 8)])
+def test_symmetric_float_sketch_several_per_block(dev, n, log2b, B):
+    """b <= 2^13 with B divisible by 2 or 4: one block builds two or four sketches from one read
+    of its wedge slab; float and double input."""
+    b = 1 << log2b
+    T = synth.random_symmetric(n, 300 + n)
+    h, g = tsk.cs_hashes(40 + n, B, log2b, [n], dev)
+    ho, go = O.cs_hashes(40 + n, B, log2b, [n])
+    S32 = tsk.sketch_tensor(t32(T, dev), h, g, log2b).cpu().numpy()
+    S64in = tsk.sketch_tensor(torch.tensor(T, device=dev), h, g, log2b).cpu().numpy()
+    T32 = T.astype(np.float32).astype(np.float64)
+    for m in range(B):
+        assert rel(S32[m], O.sketch_tensor_sym(T32, ho[m, 0], go[m, 0], b)) < 1e-5
+        assert rel(S64in[m], O.sketch_tensor_sym(T, ho[m, 0], go[m, 0], b)) < 1e-5
+
+
 @pytest.mark.parametrize("dims,log2b", [((7, 5, 3), 8), ((40, 33, 29), 12), ((50, 40, 30), 15)])
 def test_asymmetric_sketch(dev, dims, log2b):
     b = 1 << log2b
