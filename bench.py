@@ -37,9 +37,6 @@ CFG = dict(n=400, k=20, noise=0.005, B=10, log2b=14, L=50, T=30, seed=1)
 WORKLOAD = ("dense symmetric FP32 n=400 (256 MB), k=20 planted orthonormal, lambda~U[1,2], "
             "noise 0.005; B=10, b=2^14, L=50, T=30, full sketch build + power method + deflation")
 
-# FP32 lanes per SM on GB300 and its SM count / maximum SM clock (used for the ALU roof)
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-SMEM_BYTES_PER_CLK = 128
 
 
 def fft_flops(logn: int) -> float:
@@ -95,6 +92,33 @@ def peaks():
         with open(path) as f:
             return json.load(f), "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def measure_roofs(tsk, dev, reps: int = 5) -> dict:
+    """On-chip roofs measured on this GPU in this run by the library's micro-kernels (best of
+    `reps` event-timed launches each): FP32 FMA TFLOP/s, shared-memory load GB/s, and random-bucket
+    int32 shared-atomic adds/s (the colliding build's scatter)."""
+    import torch
+    sink = torch.zeros(16, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"sms": torch.cuda.get_device_properties(dev).multi_processor_count}
+    for key, kind, iters, unit in (("fp32_tflops", tsk.PEAK_FMA, 4096, 1e12),
+                                   ("smem_gbs", tsk.PEAK_SMEM, 2048, 1e9),
+                                   ("shared_atomics_per_s", tsk.PEAK_ATOMS, 4096, 1.0)):
+        tsk.peak_launch(kind, 64, sink)
+        best = float("inf")
+        for _ in range(reps):
+            e0.record(stream)
+            tsk.peak_launch(kind, iters, sink)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            best = min(best, e0.elapsed_time(e1))
+        out[key] = tsk.peak_work(kind, iters, dev) / (best / 1e3) / unit
+    out["how"] = ("library micro-kernels (tsk_peak_launch), best of %d CUDA-event-timed launches: "
+                  "8 FMA chains/thread; conflict-free 16-byte shared loads; random-bucket int32 "
+                  "shared atomicAdd with the old value consumed, 128 KB histogram per SM" % reps)
+    return out
 
 
 # ------------------------------------------------------------------ clocks
@@ -153,11 +177,38 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ inputs
-def make_inputs(cfg):
+def make_inputs(cfg, planted: bool = False):
     import synth
     T, lam, A = synth.planted_symmetric(cfg["n"], cfg["k"], cfg["noise"], cfg["seed"], dtype=np.float32)
     U0 = synth.gaussian_inits(cfg["k"], cfg["L"], cfg["n"], cfg["seed"] + 1).astype(np.float32)
-    return T, U0
+    return (T, U0, lam, A) if planted else (T, U0)
+
+
+def paper_synthetic_device(n: int, sigma: float, seed: int, dev):
+    """The paper's synthetic tensor (Sec. 5.1) generated on the GPU from a seeded generator:
+    T = sum_i lam_i v_i^(x)3 + E with lam_i = 1/i normalised, V orthonormal (QR of a Gaussian
+    matrix), E symmetric with one N(0, (sigma / n^1.5)^2) draw per sorted index triple; float32.
+    Returns (T on the device, V as a host FP64 array)."""
+    import torch
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    V, _ = torch.linalg.qr(torch.randn((n, n), generator=gen, device=dev, dtype=torch.float64))
+    lam = 1.0 / torch.arange(1, n + 1, device=dev, dtype=torch.float64)
+    lam /= torch.linalg.vector_norm(lam)
+    noise = torch.randn((n, n, n), generator=gen, device=dev, dtype=torch.float32)
+    flat = noise.view(-1)
+    T = torch.empty((n, n, n), device=dev, dtype=torch.float32)
+    jj, kk = torch.meshgrid(torch.arange(n, device=dev), torch.arange(n, device=dev), indexing="ij")
+    V32 = V.float()
+    std = sigma / n ** 1.5
+    for i in range(n):
+        lo = torch.clamp(torch.minimum(jj, kk), max=i)
+        hi = torch.clamp(torch.maximum(jj, kk), min=i)
+        mid = i + jj + kk - lo - hi
+        sig_i = (V32 * (lam * V[i]).float()[None, :]) @ V32.T
+        T[i] = sig_i + std * flat[(lo * n + mid) * n + hi]
+    del noise, flat
+    return T, V.cpu().numpy()
 
 
 # ------------------------------------------------------------------ CPU oracle timing
@@ -250,7 +301,7 @@ def run_ours(args):
     cfg = dict(CFG)
     n, k, B, log2b, L, T_it = cfg["n"], cfg["k"], cfg["B"], cfg["log2b"], cfg["L"], cfg["T"]
     b = 1 << log2b
-    T_host, U0_host = make_inputs(cfg)
+    T_host, U0_host, lam_true, A_true = make_inputs(cfg, planted=True)
     T_d = torch.from_numpy(T_host).to(dev)
     U0_d = torch.from_numpy(U0_host).to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -287,6 +338,8 @@ def run_ours(args):
     contractions = k * L * T_it
     value = whole_job_rate(contractions, world, args.steps, t_ms)
 
+    # roofs measured on this GPU now, by the library's micro-kernels
+    roofs = measure_roofs(tsk, dev)
     # dominant kernel: the fused contraction kernel in its power-step launch shape (B x L blocks)
     h, g = tsk.cs_hashes(cfg["seed"], B, log2b, [n], dev)
     S = tsk.sketch_tensor(T_d, h, g, log2b)
@@ -304,11 +357,14 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     k_ms = e0.elapsed_time(e1) / reps
     flops = B * L * contraction_flops(log2b)
-    clock_mhz = SM_MAX_MHZ
-    alu_peak = SMS * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
-    smem_peak = SMS * SMEM_BYTES_PER_CLK * clock_mhz * 1e6 / 1e9
+    alu_peak = roofs["fp32_tflops"]
+    smem_peak = roofs["smem_gbs"]
     achieved_tf = flops / (k_ms / 1e3) / 1e12
     smem_gbs = B * L * contraction_smem_bytes(log2b) / (k_ms / 1e3) / 1e9
+    # the same algorithmic count over the whole timed step: k L T power updates of B sketches
+    # (4 FFTs each) plus k L selections (2 forward FFTs per sketch)
+    step_flops = k * L * B * (T_it * contraction_flops(log2b) + 2 * fft_flops(log2b))
+    in_step_tf = step_flops / (per_step_ms / 1e3) / 1e12
 
     # sketch build: wedge entries read once (4 B each) + hash tables
     pk, pk_kind = peaks()
@@ -327,6 +383,13 @@ def run_ours(args):
         bt.append(e0.elapsed_time(e1))
     b_ms = statistics.median(bt)
     build_gbs = build_bytes / (b_ms / 1e3) / 1e9
+    build_adds = B * W / (b_ms / 1e3)   # one shared-memory add per (wedge entry, sketch)
+
+    # recovery of the planted components by this run's Alg. 1 (the last timed step)
+    resid, wrong = e1_accuracy(T_d, res["lam"], res["V"], A_true, k)
+    align = np.abs(A_true.T @ res["V"].double().cpu().numpy().T).max(axis=1)
+
+    e1 = None if args.no_e1_cell else e1_cell(tsk, dev, args)
 
     # end to end through the public call with pinned host buffers
     T_pin = torch.from_numpy(T_host).pin_memory()
@@ -361,24 +424,40 @@ def run_ours(args):
         "sketch_contractions_per_s": value * B,
         "roofline": {"kernel": "contract_kernel<14, MODE_IUU, 2> (grid B x 4 classes x L = 2000 blocks)",
                      "bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": achieved_tf / alu_peak,
+                     "frac": achieved_tf / alu_peak, "peak_kind": "measured (FP32 FMA micro-kernel, this run)",
                      "traffic": measured_traffic("contract_kernel_n400_b16384.md"),
                      "traffic_note": "DRAM bytes per launch from the ncu capture in profiles/ (null if the kernel changed since)",
                      "launch_ms": k_ms, "flops_per_launch": flops,
                      "flops_executed_per_launch": B * L * contraction_flops_executed(log2b),
                      "flops_basis": "4 length-b FFTs x 5 b log2 b per sketch-contraction",
-                     "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {clock_mhz:.0f} MHz",
+                     "in_step": {"achieved": in_step_tf, "frac": in_step_tf / alu_peak,
+                                 "flops_per_step": step_flops,
+                                 "basis": "the same count over the timed step (all launches) / ms_per_step"},
                      "smem": {"achieved": smem_gbs, "peak": smem_peak, "unit": "GB/s",
-                              "frac": smem_gbs / smem_peak}},
+                              "frac": smem_gbs / smem_peak, "peak_kind": "measured (shared-load micro-kernel, this run)"}},
         "sketch_build": {"bound": "hbm", "achieved": build_gbs, "peak": pk["hbm_gbs"],
                          "unit": "GB/s", "frac": build_gbs / pk["hbm_gbs"], "launch_ms": b_ms,
-                         "bytes": build_bytes, "peak_kind": pk_kind},
+                         "bytes": build_bytes, "peak_kind": pk_kind,
+                         "atomic_roof": {"achieved": build_adds, "peak": roofs["shared_atomics_per_s"],
+                                         "unit": "shared int32 adds/s", "frac": build_adds / roofs["shared_atomics_per_s"],
+                                         "peak_kind": "measured (random-bucket shared-atomic micro-kernel, this run)",
+                                         "basis": "one add per (wedge entry, sketch): B n(n+1)(n+2)/6"}},
+        "roofs": roofs,
         "e2e": {"value": contractions / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "s_per_step": e2e_s},
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": launches_per_step * args.steps,
-        "results": {"lambda_head": [round(float(x), 6) for x in res["lam"][:5].cpu()]},
+        "results": {"lambda_head": [round(float(x), 6) for x in res["lam"][:5].cpu()],
+                    "planted_lambda_head": [round(float(x), 6) for x in lam_true[:5]],
+                    "squared_residual": resid, "relative_squared_residual":
+                        resid / float(torch.linalg.vector_norm(T_d, dtype=torch.float64) ** 2),
+                    "planted_recovered": int((align > 0.9).sum()), "planted_max_alignment": float(align.max()),
+                    "note": "at n=400, noise 0.005 and b=2^14 the per-bucket sketch noise (~||T||_F / sqrt(b)) "
+                            "exceeds a planted component's coordinates, so this configuration's estimates "
+                            "do not align with the planted vectors; the e1_cell key is a configuration that "
+                            "recovers them"},
+        "e1_cell": e1,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -543,7 +622,8 @@ def run_lda(args):
     U = torch.nn.functional.normalize(U0[0], dim=1).contiguous()
     k_ms, _ = timed(lambda: tsk.contract_iuu(FS, S, h, g, U), reps=50)
     flops = B * L * contraction_flops(log2b)
-    alu_peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roofs = measure_roofs(tsk, dev)
+    alu_peak = roofs["fp32_tflops"]
     achieved_tf = flops / (k_ms / 1e3) / 1e12
     wedge = k * (k + 1) * (k + 2) // 6
     nnz = int(c["indptr"][-1])
@@ -757,6 +837,51 @@ def e1_accuracy(T_d, lam_hat, V_hat, V_true, k):
     return resid, wrong
 
 
+def e1_cell(tsk, dev, args):
+    """One cell of the paper's synthetic grid (Sec. 5.1, Tables 2 and 4): B = 20, b = 2^14 on the
+    full-rank n = 1000 tensor (generated on the GPU), top 10 by Alg. 1 with L = T = 30: build and
+    Alg. 1 times, squared residual and wrong vectors next to the paper's figures for that cell."""
+    import torch
+    c = dict(E1_CFG)
+    n, k, L, T_it, B, lb = c["n"], c["k"], c["L"], c["T"], 20, 14
+    t0 = time.perf_counter()
+    T_d, V = paper_synthetic_device(n, c["sigma"], c["seed"], dev)
+    torch.cuda.synchronize(dev)
+    gen_s = time.perf_counter() - t0
+    import synth
+    U0 = torch.from_numpy(synth.gaussian_inits(k, L, n, c["seed"] + 3).astype(np.float32)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h, g = tsk.cs_hashes(c["seed"], B, lb, [n], dev)
+    S = tsk.sketch_tensor(T_d, h, g, lb)
+    res = tsk.robust_power_method(S, h, g, U0, T_it)
+    torch.cuda.synchronize(dev)
+    reps = max(1, min(args.steps, 3))
+    e0.record(stream)
+    for _ in range(reps):
+        S = tsk.sketch_tensor(T_d, h, g, lb)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    b_ms = e0.elapsed_time(e1) / reps
+    e0.record(stream)
+    for _ in range(reps):
+        res = tsk.robust_power_method(S, h, g, U0, T_it)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    r_ms = e0.elapsed_time(e1) / reps
+    tsk.check_status(dev)
+    resid, wrong = e1_accuracy(T_d, res["lam"], res["V"], V, k)
+    pm, pr, pw = PAPER_E1[(B, lb)]
+    del T_d
+    torch.cuda.empty_cache()
+    return {"workload": "paper's synthetic grid cell: full-rank symmetric n=1000 FP32 (4 GB, generated "
+                        "on the GPU), lam_i=1/i normalised, noise 0.01/n^1.5; B=20, b=2^14, top 10, L=T=30",
+            "build_ms": b_ms, "rtpm_ms": r_ms, "contractions_per_s": k * L * T_it / (r_ms / 1e3),
+            "squared_residual": resid, "wrong_vectors": wrong, "generation_s": gen_s,
+            "paper": {"minutes": pm, "residual": pr, "wrong_vectors": pw,
+                      "hardware": "one 2.67 GHz Xeon X5550 core, build excluded"}}
+
+
 def run_e1(args):
     """The paper's synthetic timing/accuracy grid (Sec. 5.1, Table 2 and Table 4): a full-rank
     symmetric n = 1000 tensor (4 GB), lam_i = 1/i normalised, noise sigma / n^1.5; the top 10
@@ -903,7 +1028,8 @@ def run_orderp(args):
     torch.cuda.synchronize(dev)
     k_ms = e0.elapsed_time(e1) / reps
     flops = B * L * orderp_flops(log2b, p)
-    alu_peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roofs = measure_roofs(tsk, dev)
+    alu_peak = roofs["fp32_tflops"]
     achieved = flops / (k_ms / 1e3) / 1e12
     # the wedge build (n^4/24 entries of the 400 MB tensor), after an L2 flush
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -967,7 +1093,7 @@ def run_orderp(args):
                          "traffic_note": "DRAM bytes per launch from the ncu capture in profiles/ (null if the kernel changed since)",
                          "launch_ms": k_ms, "flops_per_launch": flops,
                          "flops_basis": "2 (p-1) length-b FFTs x 5 b log2 b per sketch-contraction",
-                         "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz"},
+                         "peak_kind": "measured (FP32 FMA micro-kernel, this run)"},
             "sketch_build": {"bound": "hbm", "achieved": build_bytes / (b_ms / 1e3) / 1e9,
                              "peak": pk["hbm_gbs"], "unit": "GB/s",
                              "frac": build_bytes / (b_ms / 1e3) / 1e9 / pk["hbm_gbs"],
@@ -1071,6 +1197,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e1-cell", action="store_true",
+                    help="skip the paper-grid cell (n=1000, B=20, b=2^14) in the default workload")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

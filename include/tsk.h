@@ -68,7 +68,11 @@ int tsk_ctx_create(int device, void* stream, tsk_ctx** out);
 /* Free the context's workspace and the context itself.  Synchronises its stream first. */
 int tsk_ctx_destroy(tsk_ctx* ctx);
 
-/* Re-bind the context to another stream of the same device (cheap; no synchronisation). */
+/* Re-bind the context to another stream of the same device (no host synchronisation).  The
+ * context's workspace and status word are shared by the streams it is bound to, so work
+ * enqueued after the re-binding waits on the device for the work already enqueued on the
+ * previous stream (an event recorded there).  While either stream is being captured into a CUDA
+ * graph nothing is recorded: the capturing caller orders its streams itself. */
 int tsk_ctx_set_stream(tsk_ctx* ctx, void* stream);
 
 /* Synchronise the context's stream, then return and clear the first device-side error
@@ -77,6 +81,19 @@ int tsk_ctx_status(tsk_ctx* ctx);
 
 /* Static, human-readable text for a status code. */
 const char* tsk_strerror(int status);
+
+/* ---------------------------------------------------------------- measured roofs (no counterpart in the paper) */
+
+/* Micro-kernels for the roofs the kernels are measured against.  TSK_PEAK_FMA: FP32 FMA issue
+ * (8 independent chains per thread, work in flops); TSK_PEAK_SMEM: conflict-free 16-byte shared
+ * loads (work in bytes); TSK_PEAK_ATOMS: random-bucket int32 shared-memory adds that return the
+ * old value, into a 128 KB histogram per SM as in the colliding build (work in adds).
+ * tsk_peak_launch enqueues one launch of `iters` iterations on the context's stream (sink: a
+ * device scratch word the kernels never actually write); the caller times it with events and
+ * divides tsk_peak_work's figure for the same (kind, iters) by the time. */
+enum tsk_peak_kind { TSK_PEAK_FMA = 0, TSK_PEAK_SMEM = 1, TSK_PEAK_ATOMS = 2 };
+int tsk_peak_launch(tsk_ctx* ctx, int kind, int iters, void* sink);
+int tsk_peak_work(tsk_ctx* ctx, int kind, int iters, double* work);
 
 /* ---------------------------------------------------------------- hashing (Sec. 2, Sec. 3.3, Prop. 2) */
 
@@ -160,7 +177,9 @@ int contract_iuu(tsk_ctx* ctx, const float* FS, const float* S, const int32_t* h
  * used.  The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  * and should come before any stream capture.  Returns TSK_EUNSUPPORTED when the scratch,
  * L*B*n*4 + L*B*4 + L*4 bytes with each part rounded up to 256, would exceed 4 MiB.  All calls
- * share the array: calls whose kernels overlap on the GPU (e.g. on two streams) race. */
+ * share the array: calls whose kernels overlap on the GPU (e.g. on two streams) race.  Having no
+ * context, it records no device status: a zero or non-finite input vector is not reported (its
+ * output row is computed from it as given). */
 int contract_iuu_static(const float* FS, const float* S, const int32_t* h, const uint8_t* g,
                         int B, int log2b, const float* U, int L, int64_t n, float* Vmed,
                         void* stream);

@@ -7,7 +7,8 @@ contract_uuu, robust_power_method, decompose_symmetric; asymmetric sketches: ske
 contract_ivw, cp_sketch_loss (+ CPSketchLoss autograd function), cp_als_solve, cp_als_step;
 many problems: BatchPlan (tsk_batch_create / tsk_batch_run); spectral LDA (Alg. 3):
 lda_m2_apply, lda_whiten, lda_whitened_m3, lda_sketch_m3, lda_recover, spectral_lda; order-p
-symmetric sketches: cs_hashes_p, sketch_tensor_p, contract_p, robust_power_method_p.
+symmetric sketches: cs_hashes_p, sketch_tensor_p, contract_p, robust_power_method_p; roof
+micro-kernels: peak_launch, peak_work.
 """
 from .api import (cs_hashes, sketch_tensor, sketch_fft, sketch_rank1,  # noqa: F401
                   contract_iuu, contract_uuu, robust_power_method, decompose_symmetric,
@@ -15,5 +16,6 @@ from .api import (cs_hashes, sketch_tensor, sketch_fft, sketch_rank1,  # noqa: F
                   contract_ivw, cp_sketch_loss, CPSketchLoss, cp_loss, cp_als_solve, cp_als_step,
                   BatchPlan, lda_m2_apply, lda_whiten, lda_whitened_m3, lda_sketch_m3,
                   lda_recover, spectral_lda, cs_hashes_p, sketch_tensor_p, contract_p,
-                  robust_power_method_p, robust_power_method_p_launches)
+                  robust_power_method_p, robust_power_method_p_launches, peak_launch, peak_work,
+                  PEAK_FMA, PEAK_SMEM, PEAK_ATOMS)
 from ._lib import TskError, LIB_PATH, load as load_library  # noqa: F401

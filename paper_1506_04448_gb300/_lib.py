@@ -27,6 +27,8 @@ SIGNATURES = {
     "tsk_ctx_set_stream": (_I, [_P, _P]),
     "tsk_ctx_status": (_I, [_P]),
     "tsk_strerror": (ctypes.c_char_p, [_I]),
+    "tsk_peak_launch": (_I, [_P, _I, _I, _P]),
+    "tsk_peak_work": (_I, [_P, _I, _I, ctypes.POINTER(_D)]),
     "cs_hashes": (_I, [_P, _U64, _I, _I, _I, _P, _P, _P]),
     "sketch_tensor": (_I, [_P, _P, _I, _I, _P, _P, _P, _I, _I, _P, _I, _I]),
     "sketch_fft": (_I, [_P, _P, _P, _I, _I, _I]),

@@ -79,6 +79,24 @@ def check_status(device: torch.device | str = "cuda") -> None:
     _lib.check("device status", rc)
 
 
+# ------------------------------------------------------------------ measured roofs
+PEAK_FMA, PEAK_SMEM, PEAK_ATOMS = 0, 1, 2
+
+
+def peak_launch(kind: int, iters: int, sink: torch.Tensor) -> None:
+    """Enqueue one roof micro-kernel launch (TSK_PEAK_*) on the current stream of sink's device."""
+    rc = _lib.load().tsk_peak_launch(_ctx(sink.device), int(kind), int(iters), _ptr(sink))
+    _lib.check("tsk_peak_launch", rc)
+
+
+def peak_work(kind: int, iters: int, device="cuda") -> float:
+    """Work of one peak_launch(kind, iters): flops, bytes or atomic adds."""
+    out = ctypes.c_double()
+    rc = _lib.load().tsk_peak_work(_ctx(torch.device(device)), int(kind), int(iters), ctypes.byref(out))
+    _lib.check("tsk_peak_work", rc)
+    return out.value
+
+
 # ------------------------------------------------------------------ hashing
 def cs_hashes(seed: int, B: int, log2b: int, dims, device="cuda"):
     """Hash tables of B sketches: (h int32 [B][M][nmax], g uint8 [B][M][nmax])."""

@@ -113,7 +113,8 @@ extern "C" int tsk_batch_create(tsk_ctx* ctx, const tsk_problem* problems, int P
     for (int i : g.order) {
       const tsk_problem& p = problems[i];
       bytes += ws_round((size_t)L * B * p.n * 4) + ws_round((size_t)L * B * 4) +
-               ws_round(2 * (size_t)L * p.n * 4) + (p.lam_all ? 0 : ws_round((size_t)p.k * L * 4));
+               ws_round(2 * (size_t)L * p.n * 4) + (p.lam_all ? 0 : ws_round((size_t)p.k * L * 4)) +
+               ws_round((size_t)p.k * L * sizeof(double));
     }
   }
   cudaError_t e = cudaMalloc(&bt->mem, bytes ? bytes : 256);
@@ -143,6 +144,7 @@ extern "C" int tsk_batch_create(tsk_ctx* ctx, const tsk_problem* problems, int P
       d.lam_all = wc.take<float>((size_t)L * B);
       d.Ubuf = wc.take<float>(2 * (size_t)L * p.n);
       d.lam_med = p.lam_all ? p.lam_all : wc.take<float>((size_t)p.k * L);
+      d.lam_med64 = wc.take<double>((size_t)p.k * L);
       d.counters = g.counters + q * L;
       d.lambda = p.lambda;
       d.V = p.V;

@@ -23,6 +23,7 @@ struct BatchProblem {            // device-side descriptor of one problem
   float* lam_all;                // [L][B]
   float* Ubuf;                   // [2][L][n]
   float* lam_med;                // [k][L] (caller's trace or workspace)
+  double* lam_med64;             // [k][L] the same medians in FP64 (selection, deflation)
   unsigned* counters;            // [L]
   double* lambda;                // [k]
   float* V;                      // [k][n]
@@ -68,7 +69,11 @@ __global__ void __launch_bounds__(NT, contract_min_blocks(LOGB, NT))
       for (int i = threadIdx.x; i < n; i += NT) tr[i] = un[i];
     }
   } else {
-    if (threadIdx.x == 0) P.lam_med[(size_t)r * L + tau] = median_of(P.lam_all + (size_t)tau * B, B);
+    if (threadIdx.x == 0) {
+      const double med = median_of64(P.lam_all + (size_t)tau * B, B);
+      P.lam_med[(size_t)r * L + tau] = (float)med;
+      P.lam_med64[(size_t)r * L + tau] = med;
+    }
   }
   if (threadIdx.x == 0) P.counters[tau] = 0u;
 }
@@ -85,15 +90,15 @@ __global__ void __launch_bounds__(NT, 1) batch_deflate_kernel(const BatchProblem
   const int m = blockIdx.x;
   const BatchProblem& P = probs[blockIdx.y];
   const int n = P.n;
-  const float* lam_r = P.lam_med + (size_t)r * L;
+  const double* lam_r = P.lam_med64 + (size_t)r * L;
   if (threadIdx.x == 0) s_best = first_argmax(lam_r, L);
   __syncthreads();
   const int best = s_best;
-  const float lam = __ldcg(lam_r + best);
+  const double lam = __ldcg(lam_r + best);
   const float* u = P.Ubuf + ((size_t)(T & 1) * L + best) * n;
   if (m == 0) {
     if (threadIdx.x == 0) {
-      P.lambda[r] = (double)lam;
+      P.lambda[r] = lam;
       if (P.tau) P.tau[r] = best;
     }
     for (int i = threadIdx.x; i < n; i += NT) P.V[(size_t)r * n + i] = __ldcg(u + i);

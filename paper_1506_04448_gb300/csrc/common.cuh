@@ -63,6 +63,8 @@ struct tsk_ctx {
   cudaStream_t aux[kCtxAuxStreams];
   cudaEvent_t ev_fork;
   cudaEvent_t ev_join[kCtxAuxStreams];
+  // orders a newly bound stream after the previous one (created on the first re-binding)
+  cudaEvent_t ev_switch;
 };
 
 // Grow the context workspace to at least `bytes` (synchronising the stream when it grows).

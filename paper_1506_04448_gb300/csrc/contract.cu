@@ -273,7 +273,8 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
   const int P = 1 << logp;
   const size_t need = 2 * ws_round(B * b * sizeof(float2)) + ws_round((size_t)L * B * P * n * 4) +
                       ws_round((size_t)L * B * P * 4) + ws_round(2 * (size_t)L * n * 4) +
-                      ws_round((size_t)k * L * 4) + ws_round((size_t)L * 4) +
+                      ws_round((size_t)k * L * 4) + ws_round((size_t)k * L * sizeof(double)) +
+                      ws_round((size_t)L * 4) +
                       (P > 1 ? ws_round(B * b * sizeof(float2)) : 0);
   int rc = tsk_ws_reserve(ctx, need);
   if (rc != TSK_OK) return rc;
@@ -286,6 +287,7 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
   float* lam_all = wc.take<float>((size_t)L * B * P);
   float* Ubuf = wc.take<float>(2 * (size_t)L * n);
   float* lam_med = lam_all_out ? lam_all_out : wc.take<float>((size_t)k * L);
+  double* lam_med64 = wc.take<double>((size_t)k * L);   // selection and deflation in FP64
   unsigned* counters = wc.take<unsigned>(L);
   float2* Gdefl = P > 1 ? wc.take<float2>(B * b) : nullptr;
   cudaStream_t st = ctx->stream;
@@ -336,6 +338,7 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
         a.Unext = next;
         a.Vmed = nullptr;
         a.lam_med = nullptr;
+        a.lam_med64 = nullptr;
         if ((rc = launch_contract(log2b, logp, MODE_IUU, a, gs)) != TSK_OK) return rc;
         cur = next;
       }
@@ -344,12 +347,13 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
       a.normalize_input = 0;
       a.Unext = nullptr;
       a.lam_med = lam_med + (size_t)r * L + tau0;
+      a.lam_med64 = lam_med64 + (size_t)r * L + tau0;
       if ((rc = launch_contract(log2b, logp, MODE_UUU, a, gs)) != TSK_OK) return rc;
       TSK_CUDA(cudaEventRecord(ctx->ev_join[s], gs));
       TSK_CUDA(cudaStreamWaitEvent(st, ctx->ev_join[s], 0));
     }
     d.Ufinal = U_iters ? U_iters + ((size_t)r * T + (T - 1)) * L * n : Ubuf + (size_t)(T & 1) * L * n;
-    d.lam_med = lam_med + (size_t)r * L;
+    d.lam_med = lam_med64 + (size_t)r * L;
     d.round = r;
     if ((rc = launch_deflate(log2b, logp, d, B, st)) != TSK_OK) return rc;
   }

@@ -44,6 +44,7 @@ struct ContractArgs {
   float* Vmed;           // [L][n]    median over sketches, or NULL
   float* Unext;          // [L][n]    normalised median (power step), or NULL
   float* lam_med;        // [L]       median of lam_all, or NULL
+  double* lam_med64;     // [L]       the same median in FP64 (eigenvalue bookkeeping), or NULL
   unsigned* counters;    // [L]       arrival counters, zero between launches
   int* status;
 };
@@ -252,12 +253,33 @@ __device__ __forceinline__ float median_of(const float* x, int B, int parts = 1)
   return small_median(vals, B);
 }
 
+// The same median in FP64: the P shares of each sketch's value are summed and the middle values
+// averaged in double, so the eigenvalue estimate is not rounded to float again.
+__device__ __forceinline__ double median_of64(const float* x, int B, int parts = 1) {
+  double vals[kMaxB];
+  for (int c = 0; c < B; ++c) {
+    double v = (double)__ldcg(x + (size_t)c * parts);
+    for (int q = 1; q < parts; ++q) v += (double)__ldcg(x + (size_t)c * parts + q);
+    vals[c] = v;
+  }
+  return small_median(vals, B);
+}
+
+// lambda^ D as lambda_hi D + lambda_lo D with lambda = lambda_hi + lambda_lo (two floats, about
+// 48 significant bits): the FP64 eigenvalue enters the FP32 sketch update unrounded; the only
+// rounding is that of the product.
+__device__ __forceinline__ float2 scale_by_double(float2 D, double lam) {
+  const float hi = (float)lam;
+  const float lo = (float)(lam - (double)hi);
+  return make_float2(fmaf(D.x, hi, D.x * lo), fmaf(D.y, hi, D.y * lo));
+}
+
 // Deflation of one sketch by lambda^ u(x)u(x)u (Alg. 1, deflation step; Sec. 3.3):
 //   U = F s~_u,  D = lambda^ U^3,  FS[m] -= D,  S[m] -= F^-1 D.
 template <int LOGB, int NT = threads_for_logb(LOGB)>
 __device__ __forceinline__ void deflate_one(float2* A, const float2* tw, float2* FSm, float2* Sm,
                                             const int32_t* hm,
-                                            const uint8_t* gm, const float* u, int n, float lam) {
+                                            const uint8_t* gm, const float* u, int n, double lam) {
   constexpr int b = 1 << LOGB;
   const int tid = threadIdx.x;
   for (int i = tid; i < padded_len(b); i += NT) A[i] = make_float2(0.f, 0.f);
@@ -272,7 +294,7 @@ __device__ __forceinline__ void deflate_one(float2* A, const float2* tw, float2*
   block_fft<LOGB, NT, -1>(A, tw);
   for (int f = tid; f < b; f += NT) {
     const float2 U = A[pad_idx(f)];
-    const float2 D = cscale(cmul(cmul(U, U), U), lam);
+    const float2 D = scale_by_double(cmul(cmul(U, U), U), lam);
     FSm[f] = csub(__ldcg(FSm + f), D);
     A[pad_idx(f)] = D;
   }
@@ -291,7 +313,7 @@ __device__ __forceinline__ void deflate_one(float2* A, const float2* tw, float2*
 template <int LOGB, int LOGP, int NT>
 __device__ __forceinline__ void deflate_part(float2* A, const float2* tw, float2* FSm, float2* Gm,
                                              const int32_t* hm, const uint8_t* gm, const float* u,
-                                             int n, float lam, int part) {
+                                             int n, double lam, int part) {
   constexpr int b = 1 << LOGB;
   constexpr int LOGM = LOGB - LOGP;
   constexpr int M = 1 << LOGM;
@@ -311,7 +333,7 @@ __device__ __forceinline__ void deflate_part(float2* A, const float2* tw, float2
   block_fft<LOGM, NT, -1>(A, tw);
   for (int f = tid; f < M; f += NT) {
     const float2 U = A[pad_idx(f)];
-    const float2 D = cscale(cmul(cmul(U, U), U), lam);
+    const float2 D = scale_by_double(cmul(cmul(U, U), U), lam);
     FSm[P * f + part] = csub(__ldcg(FSm + P * f + part), D);
     A[pad_idx(f)] = D;
   }
@@ -373,11 +395,12 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB - LOGP), 1) fft_split_ke
 }
 
 // First index of the maximum of x[0..L) (the selection tau* of Alg. 1).
-__device__ __forceinline__ int first_argmax(const float* x, int L) {
+template <typename V>
+__device__ __forceinline__ int first_argmax(const V* x, int L) {
   int best = 0;
-  float bv = __ldcg(x);
+  V bv = __ldcg(x);
   for (int t = 1; t < L; ++t) {
-    const float v = __ldcg(x + t);
+    const V v = __ldcg(x + t);
     if (v > bv) {
       bv = v;
       best = t;
@@ -416,7 +439,11 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB - LOGP),
   if (threadIdx.x == 0) a.lam_all[share] = lam;
   if (!arrive_is_last(&a.counters[tau], (unsigned)(B * P), &s_last)) return;
   if (threadIdx.x == 0) {
-    if (a.lam_med) a.lam_med[tau] = median_of(a.lam_all + (size_t)tau * B * P, B, P);
+    if (a.lam_med || a.lam_med64) {
+      const double med = median_of64(a.lam_all + (size_t)tau * B * P, B, P);
+      if (a.lam_med) a.lam_med[tau] = (float)med;
+      if (a.lam_med64) a.lam_med64[tau] = med;
+    }
     a.counters[tau] = 0u;
   }
   if constexpr (MODE == MODE_IUU) {
@@ -439,7 +466,7 @@ struct DeflateArgs {
   const uint8_t* g;
   int n, L;
   const float* Ufinal;      // [L][n] final iterates of the round
-  const float* lam_med;     // [L] eigenvalue medians of the round
+  const double* lam_med;    // [L] eigenvalue medians of the round (FP64)
   int round;
   double* lambda_out;       // [k]
   float* Vout;              // [k][n]
@@ -461,11 +488,11 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB - LOGP), 1) deflate_kern
   if (threadIdx.x == 0) s_best = first_argmax(a.lam_med, a.L);
   __syncthreads();
   const int best = s_best;
-  const float lam = a.lam_med[best];
+  const double lam = a.lam_med[best];
   const float* u = a.Ufinal + (size_t)best * n;
   if (blockIdx.x == 0) {
     if (threadIdx.x == 0) {
-      a.lambda_out[a.round] = (double)lam;
+      a.lambda_out[a.round] = lam;
       if (a.tau_out) a.tau_out[a.round] = best;
     }
     for (int i = threadIdx.x; i < n; i += NT) a.Vout[(size_t)a.round * n + i] = u[i];

@@ -93,6 +93,7 @@ extern "C" int tsk_ctx_destroy(tsk_ctx* ctx) {
     cudaEventDestroy(ctx->ev_join[i]);
   }
   if (ctx->n_aux > 0) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_switch) cudaEventDestroy(ctx->ev_switch);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->status) cudaFree(ctx->status);
   free(ctx);
@@ -101,7 +102,29 @@ extern "C" int tsk_ctx_destroy(tsk_ctx* ctx) {
 
 extern "C" int tsk_ctx_set_stream(tsk_ctx* ctx, void* stream) {
   if (!ctx) return TSK_EINVAL;
-  ctx->stream = static_cast<cudaStream_t>(stream);
+  cudaStream_t next = static_cast<cudaStream_t>(stream);
+  if (next == ctx->stream) return TSK_OK;
+  // The workspace and the status word serve every stream the context is bound to, so work
+  // enqueued from now on waits for the work already queued on the previous stream (an event
+  // recorded there).  Not while either stream is being captured into a graph: a capture cannot
+  // wait on uncaptured work, and the capturing caller orders its streams itself.
+  DeviceGuard guard(ctx->device);
+  if (!guard.ok) return TSK_ECUDA;
+  cudaStreamCaptureStatus cap_next = cudaStreamCaptureStatusNone;
+  cudaStreamCaptureStatus cap_prev = cudaStreamCaptureStatusNone;
+  bool order = cudaStreamIsCapturing(next, &cap_next) == cudaSuccess &&
+               cap_next == cudaStreamCaptureStatusNone;
+  if (order)
+    order = cudaStreamIsCapturing(ctx->stream, &cap_prev) == cudaSuccess &&
+            cap_prev == cudaStreamCaptureStatusNone;
+  cudaGetLastError();   // a refused query only means: do not order
+  if (order) {
+    if (!ctx->ev_switch)
+      TSK_CUDA(cudaEventCreateWithFlags(&ctx->ev_switch, cudaEventDisableTiming));
+    TSK_CUDA(cudaEventRecord(ctx->ev_switch, ctx->stream));
+    TSK_CUDA(cudaStreamWaitEvent(next, ctx->ev_switch, 0));
+  }
+  ctx->stream = next;
   return TSK_OK;
 }
 

@@ -1,0 +1,93 @@
+// Micro-kernels that measure the on-chip roofs the contraction and build kernels are judged
+// against: FP32 FMA issue rate, shared-memory load bandwidth, and the rate of random-bucket
+// int32 shared-memory atomics (the build's scatter).  The paper has no counterpart; the caller
+// times each launch with events on the context's stream and divides the work by the time.
+#include "common.cuh"
+
+namespace {
+
+// 8 independent FMA chains per thread, 16 steps each per iteration: 256 flops per iteration.
+__global__ void __launch_bounds__(256) peak_fma_kernel(float* sink, int iters) {
+  float a0 = threadIdx.x, a1 = a0 + 1.f, a2 = a0 + 2.f, a3 = a0 + 3.f;
+  float a4 = a0 + 4.f, a5 = a0 + 5.f, a6 = a0 + 6.f, a7 = a0 + 7.f;
+  const float m = 0.9999f, c = 1e-7f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      a0 = fmaf(a0, m, c); a1 = fmaf(a1, m, c); a2 = fmaf(a2, m, c); a3 = fmaf(a3, m, c);
+      a4 = fmaf(a4, m, c); a5 = fmaf(a5, m, c); a6 = fmaf(a6, m, c); a7 = fmaf(a7, m, c);
+    }
+  }
+  const float s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+  if (s == 1.2345f) sink[0] = s;   // never true; keeps the chains live
+}
+
+// Conflict-free 16-byte shared loads: 8 per thread per iteration (128 bytes).
+__global__ void __launch_bounds__(1024) peak_lds_kernel(float* sink, int iters) {
+  __shared__ float4 buf[2048];
+  for (int i = threadIdx.x; i < 2048; i += blockDim.x) buf[i] = make_float4(i, i, i, i);
+  __syncthreads();
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int idx = threadIdx.x & 1023;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float4 v = buf[(idx + u * 128 + i) & 2047];
+      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    }
+  }
+  if (acc.x + acc.y + acc.z + acc.w == 1.2345f) sink[0] = acc.x;
+}
+
+// Random-bucket int32 adds into a 2^15-entry shared histogram (128 KB, one block per SM), one
+// per thread per iteration, the returned old value consumed like the build's wrap check.
+__global__ void __launch_bounds__(1024, 1) peak_atoms_kernel(int* sink, int iters) {
+  extern __shared__ int hist[];
+  constexpr int kCells = 1 << 15;
+  for (int i = threadIdx.x; i < kCells; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  uint32_t x = 0x9E3779B9u * (threadIdx.x + 1) + 7919u * blockIdx.x;
+  unsigned near = 0u;
+  for (int it = 0; it < iters; ++it) {
+    x = x * 1664525u + 1013904223u;
+    near |= (unsigned)atomicAdd(&hist[(x >> 17) & (kCells - 1)], (int)(x & 0xff)) + 0x40000000u;
+  }
+  __syncthreads();
+  if ((int)near < 0 && hist[threadIdx.x] == 12345) sink[0] = 1;
+}
+
+}  // namespace
+
+extern "C" int tsk_peak_launch(tsk_ctx* ctx, int kind, int iters, void* sink) {
+  if (!ctx || !sink || iters < 1) return TSK_EINVAL;
+  cudaStream_t st = ctx->stream;
+  switch (kind) {
+    case TSK_PEAK_FMA:
+      peak_fma_kernel<<<ctx->num_sms * 8, 256, 0, st>>>(static_cast<float*>(sink), iters);
+      break;
+    case TSK_PEAK_SMEM:
+      peak_lds_kernel<<<ctx->num_sms * 2, 1024, 0, st>>>(static_cast<float*>(sink), iters);
+      break;
+    case TSK_PEAK_ATOMS: {
+      constexpr size_t smem = (size_t)(1 << 15) * sizeof(int);
+      TSK_CUDA(tsk_smem_attr<peak_atoms_kernel>(smem));
+      peak_atoms_kernel<<<ctx->num_sms, 1024, smem, st>>>(static_cast<int*>(sink), iters);
+      break;
+    }
+    default:
+      return TSK_EINVAL;
+  }
+  TSK_CHECK_LAUNCH();
+  return TSK_OK;
+}
+
+extern "C" int tsk_peak_work(tsk_ctx* ctx, int kind, int iters, double* work) {
+  if (!ctx || !work || iters < 1) return TSK_EINVAL;
+  const double it = (double)iters;
+  switch (kind) {
+    case TSK_PEAK_FMA: *work = (double)ctx->num_sms * 8 * 256 * it * 16 * 8 * 2; return TSK_OK;
+    case TSK_PEAK_SMEM: *work = (double)ctx->num_sms * 2 * 1024 * it * 8 * 16; return TSK_OK;
+    case TSK_PEAK_ATOMS: *work = (double)ctx->num_sms * 1024 * it; return TSK_OK;
+    default: return TSK_EINVAL;
+  }
+}

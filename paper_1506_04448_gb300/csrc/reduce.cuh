@@ -32,9 +32,10 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
 
 // Median of x[0..cnt) (cnt >= 1) by insertion sort in place; mean of the two middle values
 // when cnt is even (the even-B reading of Alg. 1's median).
-__device__ __forceinline__ float small_median(float* x, int cnt) {
+template <typename V>
+__device__ __forceinline__ V small_median(V* x, int cnt) {
   for (int a = 1; a < cnt; ++a) {
-    const float key = x[a];
+    const V key = x[a];
     int c = a - 1;
     while (c >= 0 && x[c] > key) {
       x[c + 1] = x[c];
@@ -42,7 +43,7 @@ __device__ __forceinline__ float small_median(float* x, int cnt) {
     }
     x[c + 1] = key;
   }
-  return (cnt & 1) ? x[cnt / 2] : 0.5f * (x[cnt / 2 - 1] + x[cnt / 2]);
+  return (cnt & 1) ? x[cnt / 2] : (V)0.5 * (x[cnt / 2 - 1] + x[cnt / 2]);
 }
 
 // small_median on cnt values spaced `stride` apart (a column of a shared-memory scratch array,

@@ -23,7 +23,7 @@ def injective_sym_hash(n):
 
 
 # ------------------------------------------------------------------ Prop. 1 / convolution theorem
-@pytest.mark.parametrize("b", [16, 64, 1024])
+@pytest.mark.parametrize("b", [16, 64, 1024, 4096])
 def test_fft_engine_matches_direct_sums(b):
     r = synth.rng(b)
     x = r.standard_normal(b) + 1j * r.standard_normal(b)
@@ -278,6 +278,15 @@ def test_splitmix64_stream_is_the_sequential_generator():
         state = (state + Hh.GOLDEN_GAMMA) & Hh.MASK64
         assert Hh.splitmix64_output(seed, c) == Hh.mix64(state)
     assert Hh.mix64(0) == 0
+
+
+def test_splitmix64_matches_the_published_reference_stream():
+    """The first outputs of the reference SplitMix64 generator (Vigna's splitmix64.c, the
+    generator of Steele, Lea and Flood, OOPSLA 2014) started from state 0 are the published
+    test values 0xe220a8397b1dcdaf, 0x6e789e6aa1b965f4, 0x06c45d188009454f; the hash
+    coefficients are this stream's outputs, so a wrong constant or shift fails here."""
+    assert [Hh.splitmix64_output(0, c) for c in range(3)] == [
+        0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
 
 
 def test_hash_ranges_uniformity_and_sign_moments():

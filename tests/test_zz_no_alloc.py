@@ -4,7 +4,8 @@ Callers capturing a stream into a CUDA graph, or whose device memory belongs to 
 allocator, cannot let the library cudaMalloc a workspace; contract_iuu_static keeps its scratch
 in a static device array instead.  This test calls it through the C ABI twice in a row (so the
 second call sees the array as the first one left it) and compares each result with the
-workspace-based contract_iuu within the contraction tolerance (1e-5 relative, 2-norm).
+workspace-based contract_iuu within the contraction tolerance (1e-5 relative, 2-norm), and
+sampled vectors of the first call with the FP64 oracle.
 
 The file name makes pytest collect it last; it passes alone in a fresh process and after the
 other tests.
@@ -15,6 +16,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle as O
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -51,6 +53,16 @@ def test_static_scratch_matches_workspace_entry_point_on_two_calls():
         gg = got.cpu().numpy()
         for tau in range(L):
             assert np.linalg.norm(gg[tau] - w[tau]) <= 1e-5 * np.linalg.norm(w[tau]), (call, tau)
+        # and against the FP64 oracle itself (median over the B sketches), sampled vectors
+        if call == 0:
+            ho, go = O.cs_hashes(3, B, log2b, [n])
+            Sg = S.cpu().numpy().astype(np.complex128)
+            Ug = U.cpu().numpy().astype(np.float64)
+            for tau in (0, L // 2, L - 1):
+                refs = np.stack([O.contract_iuu(Sg[m], Ug[tau], ho[m, 0], go[m, 0], 1 << log2b, "fft")
+                                 for m in range(B)])
+                med = O.median_rows(refs)
+                assert np.linalg.norm(gg[tau] - med) <= 1e-5 * np.linalg.norm(med), tau
 
 
 def test_static_scratch_rejects_sizes_beyond_its_maximum():
