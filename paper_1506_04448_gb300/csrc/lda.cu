@@ -21,6 +21,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "moments_tc.cuh"
 #include "reduce.cuh"
 
 namespace tsk {
@@ -776,7 +777,8 @@ __global__ void finalize2_kernel(const float* qpart, int nqpart, const float* pa
 __global__ void finalize3_kernel(const float* part3d, int S3d, const float* part3w, int S3w,
                                  int units3_pad, const int* unit3_of,
                                  const unsigned long long* counts, const double* q,
-                                 const double* E2, int k, int kp, double alpha0, float* M3) {
+                                 const double* E2, int k, int kp, double alpha0, float* M3,
+                                 const double* tcpart, int Stc, long long tc_rows, int tc_N) {
   const int b = blockIdx.x, c = blockIdx.y;
   if (c < b) return;
   const double invD3 = 1.0 / (double)(counts[2] > 0 ? counts[2] : 1);
@@ -787,7 +789,12 @@ __global__ void finalize3_kernel(const float* part3d, int S3d, const float* part
   for (int a = threadIdx.x; a <= b; a += blockDim.x) {
     const int u = unit3_of[((b / 8) * nb + (c / 8)) * kp + a];
     double s = 0.0;
-    for (int t = 0; t < S3d; ++t) s += part3d[((size_t)t * 64 + e) * units3_pad + u];
+    if (tcpart) {   // document term from the tensor-core splits: row of pair (a, b), column c
+      const size_t row = (size_t)b * (b + 1) / 2 + a;
+      for (int t = 0; t < Stc; ++t) s += tcpart[((size_t)t * tc_rows + row) * tc_N + c];
+    } else {
+      for (int t = 0; t < S3d; ++t) s += part3d[((size_t)t * 64 + e) * units3_pad + u];
+    }
     for (int t = 0; t < S3w; ++t) s -= part3w[((size_t)t * 64 + e) * units3_pad + u];
     const double E3 = s * invD3;
     const double v = E3 - c1 * (E2[a * k + b] * q[c] + E2[a * k + c] * q[b] + E2[b * k + c] * q[a]) +
@@ -938,6 +945,10 @@ int run_orth(tsk_ctx* ctx, float* Y, int64_t V, int c, int cp, GramWs gw, double
 }  // namespace tsk
 
 using namespace tsk::lda;
+using tsk::Moments3TcArgs;
+using tsk::kMoments3TcMaxN;
+using tsk::moments3_tc_splits;
+using tsk::launch_moments3_tc;
 
 extern "C" int lda_m2_apply(tsk_ctx* ctx, const int64_t* indptr, const int32_t* idx,
                             const int32_t* cnt, int64_t D, int64_t V, double alpha0,
@@ -1061,6 +1072,16 @@ static int whitened_m3_impl(tsk_ctx* ctx, const Corpus& cps, const float* W, int
   const int S3w = (int)std::max<int64_t>(1, min64(64, (V + 2047) / 2048));
   const int64_t per_w = round_up((int)((V + S3w - 1) / S3w), kTileItems);
   const int nproj = grid_for(ctx, D);
+  // the document term of E3 on the tensor cores (3 x TF32, tcgen05) for k <= 160
+  const bool tc = round_up(k, 16) <= kMoments3TcMaxN;
+  Moments3TcArgs tca{};
+  tca.k = k;
+  tca.kp = kp;
+  tca.N = round_up(k, 16);
+  tca.npairs = (long long)k * (k + 1) / 2;
+  tca.rows_pad = (tca.npairs + 127) / 128 * 128;
+  tca.D = D;
+  const int Stc = tc ? moments3_tc_splits((int)tca.npairs, ctx->num_sms, D) : 0;
   auto carve = [&](WsCarve& wc, float*& mdoc, unsigned long long*& counts, float*& Wp, float*& P,
                    float*& R, float*& ce, float*& qpart, int*& units3, int*& unit3_of, int*& units2,
                    int*& unit2_of, float*& part3d, float*& part3w, float*& part2d, float*& part2w,
@@ -1076,7 +1097,8 @@ static int whitened_m3_impl(tsk_ctx* ctx, const Corpus& cps, const float* W, int
     unit3_of = wc.take<int>((size_t)nb * nb * kp);
     units2 = wc.take<int>(u2p);
     unit2_of = wc.take<int>((size_t)nb * kp);
-    part3d = wc.take<float>((size_t)S3d * 64 * u3p);
+    part3d = wc.take<float>(tc ? 64 : (size_t)S3d * 64 * u3p);
+    tca.part = tc ? wc.take<double>((size_t)Stc * tca.rows_pad * tca.N) : nullptr;
     part3w = wc.take<float>((size_t)S3w * 64 * u3p);
     part2d = wc.take<float>((size_t)S3d * 8 * u2p);
     part2w = wc.take<float>((size_t)S3w * 8 * u2p);
@@ -1126,8 +1148,15 @@ static int whitened_m3_impl(tsk_ctx* ctx, const Corpus& cps, const float* W, int
   MomentArgs m3w{units3, u3p, Wp, R, ce, V, per_w, kp, part3w};
   MomentArgs m2d{units2, u2p, P, nullptr, mdoc, D, per_d, kp, part2d};
   MomentArgs m2w{units2, u2p, Wp, nullptr, ce, V, per_w, kp, part2w};
-  moments_kernel<3, FROM_DOCS><<<dim3(u3p / kUnitThreads, S3d), kUnitThreads, smem1, st>>>(m3d);
-  TSK_CHECK_LAUNCH();
+  if (tc) {
+    tca.P = P;
+    tca.mdoc = mdoc;
+    tca.status = ctx->status;
+    if ((rc = launch_moments3_tc(tca, Stc, st)) != TSK_OK) return rc;
+  } else {
+    moments_kernel<3, FROM_DOCS><<<dim3(u3p / kUnitThreads, S3d), kUnitThreads, smem1, st>>>(m3d);
+    TSK_CHECK_LAUNCH();
+  }
   moments_kernel<3, FROM_WORDS><<<dim3(u3p / kUnitThreads, S3w), kUnitThreads, smem2, st>>>(m3w);
   TSK_CHECK_LAUNCH();
   moments_kernel<2, FROM_DOCS><<<dim3(u2p / kUnitThreads, S3d), kUnitThreads, smem1, st>>>(m2d);
@@ -1138,7 +1167,8 @@ static int whitened_m3_impl(tsk_ctx* ctx, const Corpus& cps, const float* W, int
                                       k, kp, q, E2);
   TSK_CHECK_LAUNCH();
   finalize3_kernel<<<dim3(k, k), 128, 0, st>>>(part3d, S3d, part3w, S3w, u3p, unit3_of, counts, q,
-                                               E2, k, kp, alpha0, M3);
+                                               E2, k, kp, alpha0, M3, tca.part, Stc, tca.rows_pad,
+                                               tca.N);
   TSK_CHECK_LAUNCH();
   return TSK_OK;
 }

@@ -120,6 +120,26 @@ def test_whitened_m3_many_splits_streamed_check():
         assert abs(np.einsum("abc,a,b,c", M3, x, x, x) - xxx) <= tol * np.abs(x).sum()
 
 
+def test_whitened_m3_tensor_core_groups_and_ragged_documents():
+    """k = 100 (5050 pair rows over 40 tiles of the tensor-core document term) and 20001
+    documents: many 1024-document compensated groups and several document splits, with a last
+    step of a single document; checked by the oracle's streamed contractions."""
+    T = tsk()
+    V, k, D = 3000, 100, 20001
+    c = synth.lda_corpus(V, k, D, 77, alpha=0.1, beta=0.02, mean_len=60)
+    a0 = k * 0.1
+    W = (synth.gaussian_matrix(V, k, 78) / np.sqrt(V)).astype(np.float32)
+    M3 = T.lda_whitened_m3(*on_dev(c), V, torch.from_numpy(W).to(dev), a0).cpu().double().numpy()
+    T.check_status(dev)
+    assert np.array_equal(M3, M3.transpose(1, 0, 2)) and np.array_equal(M3, M3.transpose(0, 2, 1))
+    for s in range(3):
+        x = synth.rng(80 + s).standard_normal(k)
+        xxx, ixx = L.whitened_m3_contract(c, W.astype(np.float64), a0, x)
+        tol = 2e-5 * np.abs(M3).max() * np.abs(x).sum() ** 2
+        np.testing.assert_allclose(np.einsum("abc,b,c->a", M3, x, x), ixx, rtol=0, atol=tol)
+        assert abs(np.einsum("abc,a,b,c", M3, x, x, x) - xxx) <= tol * np.abs(x).sum()
+
+
 def test_sketch_m3_and_paper_route():
     T = tsk()
     V, k, D = 300, 8, 1200
