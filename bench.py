@@ -413,7 +413,8 @@ def run_ours(args):
                          f"FFT engine, random sketch values) in {el:.1f} s",
                "host_cpus": os.cpu_count()}
 
-    launches_per_step = 2 + tsk.robust_power_method_launches(B, log2b, n, k, L, T_it, dev)
+    # hashes, the three build kernels (max|T| prepass, integer scatter, reduce) and Alg. 1
+    launches_per_step = 4 + tsk.robust_power_method_launches(B, log2b, n, k, L, T_it, dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": per_step_ms, "higher_is_better": True,
@@ -540,9 +541,10 @@ LDA_WORKLOAD = ("synthetic LDA corpus V=50000, k=100 topics, topic-word Dir(0.01
 
 
 def lda_launches(rpm_launches: int, q: int) -> int:
-    """Kernels of one spectral_lda call: whitening 10 + 15 (q + 1), hashes 1, whitened M3 9,
-    sketch build 1, Alg. 1 (robust_power_method_launches), recovery 5."""
-    return 10 + 15 * (q + 1) + 1 + 9 + 1 + rpm_launches + 5
+    """Kernels of one spectral_lda call: whitening 10 + 15 (q + 1), hashes 1, whitened M3 9 (its
+    document term one tensor-core launch), sketch build 3 (max|T| prepass, integer scatter,
+    reduce), Alg. 1 (robust_power_method_launches), recovery 5."""
+    return 10 + 15 * (q + 1) + 1 + 9 + 3 + rpm_launches + 5
 
 
 def oracle_lda_doc_rate(c, W, budget_s: float):
@@ -925,7 +927,7 @@ def run_e1(args):
                 tsk.check_status(dev)
                 resid, wrong = e1_accuracy(T_d, res["lam"], res["V"], V, k)
                 pm, pr, pw = PAPER_E1[(B, lb)]
-                launches += (2 + tsk.robust_power_method_launches(B, lb, n, k, L, T_it, dev)) * max(1, args.steps)
+                launches += (4 + tsk.robust_power_method_launches(B, lb, n, k, L, T_it, dev)) * max(1, args.steps)
                 grid.append({"B": B, "log2b": lb, "build_ms": b_ms, "rtpm_ms": r_ms,
                              "contractions_per_s": k * L * T_it / (r_ms / 1e3),
                              "residual": resid, "wrong_vectors": wrong,

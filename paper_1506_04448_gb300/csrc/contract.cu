@@ -104,12 +104,12 @@ int launch_deflate(int log2b, int logp, const DeflateArgs& a, int B, cudaStream_
 }
 
 template <int LOGB, int LOGP>
-static int launch_fft_split_t(const float2* S, float2* FS, int B, cudaStream_t st) {
+static int launch_fft_split_t(const float2* S, float2* FS, int B, cudaStream_t st, int cm) {
   if constexpr (LOGP > 0 && split_ok(LOGB, LOGP)) {
     constexpr int LOGM = LOGB - LOGP;
     constexpr size_t smem = (size_t)padded_len(1 << LOGM) * sizeof(float2);
     TSK_CUDA(tsk_smem_attr<fft_split_kernel<LOGB, LOGP>>(smem));
-    fft_split_kernel<LOGB, LOGP><<<B << LOGP, threads_for_logb(LOGM), smem, st>>>(S, FS);
+    fft_split_kernel<LOGB, LOGP><<<B << LOGP, threads_for_logb(LOGM), smem, st>>>(S, FS, cm);
     TSK_CHECK_LAUNCH();
     return TSK_OK;
   } else {
@@ -117,16 +117,17 @@ static int launch_fft_split_t(const float2* S, float2* FS, int B, cudaStream_t s
   }
 }
 
-int launch_fft_split(int log2b, int logp, const float2* S, float2* FS, int B, cudaStream_t st) {
+int launch_fft_split(int log2b, int logp, const float2* S, float2* FS, int B, cudaStream_t st,
+                     int cm) {
   switch (log2b * 4 + logp) {
-    case 13 * 4 + 1: return launch_fft_split_t<13, 1>(S, FS, B, st);
-    case 14 * 4 + 1: return launch_fft_split_t<14, 1>(S, FS, B, st);
-    case 14 * 4 + 2: return launch_fft_split_t<14, 2>(S, FS, B, st);
-    case 15 * 4 + 1: return launch_fft_split_t<15, 1>(S, FS, B, st);
-    case 15 * 4 + 2: return launch_fft_split_t<15, 2>(S, FS, B, st);
-    case 15 * 4 + 3: return launch_fft_split_t<15, 3>(S, FS, B, st);
-    case 16 * 4 + 2: return launch_fft_split_t<16, 2>(S, FS, B, st);
-    case 16 * 4 + 3: return launch_fft_split_t<16, 3>(S, FS, B, st);
+    case 13 * 4 + 1: return launch_fft_split_t<13, 1>(S, FS, B, st, cm);
+    case 14 * 4 + 1: return launch_fft_split_t<14, 1>(S, FS, B, st, cm);
+    case 14 * 4 + 2: return launch_fft_split_t<14, 2>(S, FS, B, st, cm);
+    case 15 * 4 + 1: return launch_fft_split_t<15, 1>(S, FS, B, st, cm);
+    case 15 * 4 + 2: return launch_fft_split_t<15, 2>(S, FS, B, st, cm);
+    case 15 * 4 + 3: return launch_fft_split_t<15, 3>(S, FS, B, st, cm);
+    case 16 * 4 + 2: return launch_fft_split_t<16, 2>(S, FS, B, st, cm);
+    case 16 * 4 + 3: return launch_fft_split_t<16, 3>(S, FS, B, st, cm);
     default: return TSK_EUNSUPPORTED;
   }
 }
@@ -296,7 +297,8 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
   if (P == 1) {
     if ((rc = launch_fft_batched(log2b, Sw, FSw, B, 0, st)) != TSK_OK) return rc;
   } else {
-    if ((rc = launch_fft_split(log2b, logp, Sw, FSw, B, st)) != TSK_OK) return rc;
+    // the workspace spectra are kept class-major (each class's frequencies contiguous)
+    if ((rc = launch_fft_split(log2b, logp, Sw, FSw, B, st, 1)) != TSK_OK) return rc;
   }
 
   ContractArgs a{};
@@ -307,6 +309,7 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
   a.n = (int)n;
   a.B = B;
   a.status = ctx->status;
+  a.fs_class_major = P > 1;
   DeflateArgs d{};
   d.FS = FSw;
   d.S = Sw;
@@ -318,6 +321,7 @@ extern "C" int robust_power_method(tsk_ctx* ctx, const float* S, const int32_t* 
   d.Vout = Vout;
   d.tau_out = tau_star;
   d.G = Gdefl;
+  d.fs_class_major = P > 1;
   for (int r = 0; r < k; ++r) {
     TSK_CUDA(cudaEventRecord(ctx->ev_fork, st));
     for (int s = 0; s < G; ++s) {

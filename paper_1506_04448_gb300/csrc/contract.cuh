@@ -45,6 +45,7 @@ struct ContractArgs {
   float* Unext;          // [L][n]    normalised median (power step), or NULL
   float* lam_med;        // [L]       median of lam_all, or NULL
   double* lam_med64;     // [L]       the same median in FP64 (eigenvalue bookkeeping), or NULL
+  int fs_class_major;    // split sketches (P > 1): FS stored per class, FS_c[f'] = FS[P f' + c]
   unsigned* counters;    // [L]       arrival counters, zero between launches
   int* status;
 };
@@ -71,13 +72,16 @@ __device__ __forceinline__ float contract_one(float2* A, float2* Eb, float* red,
                                               const float2* FSm, const float2* Sm,
                                               const int32_t* hm, const uint8_t* gm,
                                               const float* u, int n, bool normalize, int* status,
-                                              float* vout, int part = 0) {
+                                              float* vout, int part = 0, int fs_cls = 0) {
   constexpr int b = 1 << LOGB;
   constexpr int hb = b / 2;
   constexpr int LOGM = LOGB - LOGP;
   constexpr int M = 1 << LOGM;
   constexpr int hM = M / 2;
   constexpr int P = 1 << LOGP;
+  // spectrum of frequency f of this class: FS[P f + part], or FS_part[f] when class-major
+  const int fs_step = fs_cls ? 1 : P;
+  const float2* FSc = FSm + (fs_cls ? (size_t)part * M : (size_t)part);
   constexpr float inv_b = 1.f / (float)b;
   const int tid = threadIdx.x;
 
@@ -137,8 +141,8 @@ __device__ __forceinline__ float contract_one(float2* A, float2* Eb, float* red,
       const float2 cu0 = cconj(A[pad_idx(f)]);
       const float2 cu1 = cconj(A[pad_idx(f + hM)]);
       const float2 cv = cconj(Eb[pad_idx(f)]);
-      const float2 F0 = __ldcg(FSm + P * f + part);
-      const float2 F1 = __ldcg(FSm + P * (f + hM) + part);
+      const float2 F0 = __ldcg(FSc + fs_step * f);
+      const float2 F1 = __ldcg(FSc + fs_step * (f + hM));
       A[pad_idx(f)] = cmul(F0, cadd(cmul(cu0, cu0), cv));
       A[pad_idx(f + hM)] = cmul(F1, cadd(cmul(cu1, cu1), cv));
       Eb[pad_idx(f)] = cadd(cmul(F0, cu0), cmul(F1, cu1));
@@ -170,7 +174,7 @@ __device__ __forceinline__ float contract_one(float2* A, float2* Eb, float* red,
       const float2 V = Eb[pad_idx(f & (hM - 1))];
       const float2 U2 = cmul(U, U);
       const float2 Y = cadd(cscale(cmul(U2, U), 1.f / 6.f), cscale(cmul(V, U), 0.5f));
-      const float2 F = __ldcg(FSm + P * f + part);
+      const float2 F = __ldcg(FSc + fs_step * f);
       lam += F.x * Y.x + F.y * Y.y;     // Re(F conj(Y))
     }
     lam *= inv_b;
@@ -313,7 +317,7 @@ __device__ __forceinline__ void deflate_one(float2* A, const float2* tw, float2*
 template <int LOGB, int LOGP, int NT>
 __device__ __forceinline__ void deflate_part(float2* A, const float2* tw, float2* FSm, float2* Gm,
                                              const int32_t* hm, const uint8_t* gm, const float* u,
-                                             int n, double lam, int part) {
+                                             int n, double lam, int part, int fs_cls) {
   constexpr int b = 1 << LOGB;
   constexpr int LOGM = LOGB - LOGP;
   constexpr int M = 1 << LOGM;
@@ -334,7 +338,8 @@ __device__ __forceinline__ void deflate_part(float2* A, const float2* tw, float2
   for (int f = tid; f < M; f += NT) {
     const float2 U = A[pad_idx(f)];
     const float2 D = scale_by_double(cmul(cmul(U, U), U), lam);
-    FSm[P * f + part] = csub(__ldcg(FSm + P * f + part), D);
+    const size_t fi = fs_cls ? (size_t)part * M + f : (size_t)P * f + part;
+    FSm[fi] = csub(__ldcg(FSm + fi), D);
     A[pad_idx(f)] = D;
   }
   __syncthreads();
@@ -366,10 +371,12 @@ __global__ void __launch_bounds__(256) deflate_combine_kernel(float2* S, const f
 }
 
 // FS = DFT_b of the sketches S when b is split over P blocks: block (m, c) forms
-// a_c[j] = sum_q S[m][j + q M] w_b^(c (j + q M)), j < M, and FS[m][P f' + c] = DFT_M(a_c)[f'].
+// a_c[j] = sum_q S[m][j + q M] w_b^(c (j + q M)), j < M, and FS[m][P f' + c] = DFT_M(a_c)[f']
+// (or FS[m][c M + f'] when class_major: each class contiguous, read with whole sectors).
 template <int LOGB, int LOGP>
 __global__ void __launch_bounds__(threads_for_logb(LOGB - LOGP), 1) fft_split_kernel(const float2* S,
-                                                                                    float2* FS) {
+                                                                                    float2* FS,
+                                                                                    int class_major) {
   constexpr int LOGM = LOGB - LOGP;
   constexpr int NT = threads_for_logb(LOGM);
   constexpr int b = 1 << LOGB;
@@ -391,7 +398,8 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB - LOGP), 1) fft_split_ke
   __syncthreads();
   block_fft<LOGM, NT, -1>(smem, tw);
   float2* FSm = FS + (size_t)m * b;
-  for (int f = threadIdx.x; f < M; f += NT) FSm[P * f + c] = smem[pad_idx(f)];
+  for (int f = threadIdx.x; f < M; f += NT)
+    FSm[class_major ? (size_t)c * M + f : (size_t)P * f + c] = smem[pad_idx(f)];
 }
 
 // First index of the maximum of x[0..L) (the selection tau* of Alg. 1).
@@ -435,7 +443,7 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB - LOGP),
   const float lam = contract_one<LOGB, MODE, NT, LOGP>(
       A, Eb, red, tw, a.FS + (size_t)m * b, a.S + (size_t)m * b, a.h + (size_t)m * n,
       a.g + (size_t)m * n, a.U + (size_t)tau * n, n, a.normalize_input != 0, a.status,
-      MODE == MODE_IUU ? a.Vall + share * n : nullptr, part);
+      MODE == MODE_IUU ? a.Vall + share * n : nullptr, part, a.fs_class_major);
   if (threadIdx.x == 0) a.lam_all[share] = lam;
   if (!arrive_is_last(&a.counters[tau], (unsigned)(B * P), &s_last)) return;
   if (threadIdx.x == 0) {
@@ -472,6 +480,7 @@ struct DeflateArgs {
   float* Vout;              // [k][n]
   int32_t* tau_out;         // [k] or NULL
   float2* G;                // [B][P][b/P] workspace when the sketch length is split (P > 1)
+  int fs_class_major;       // FS stored per frequency class (see ContractArgs)
 };
 
 template <int LOGB, int LOGP = 0>
@@ -503,7 +512,7 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB - LOGP), 1) deflate_kern
   } else {
     deflate_part<LOGB, LOGP, NT>(smem, tw, a.FS + (size_t)m * b,
                                  a.G + ((size_t)m * P + part) * (b / P), a.h + (size_t)m * n,
-                                 a.g + (size_t)m * n, u, n, lam, part);
+                                 a.g + (size_t)m * n, u, n, lam, part, a.fs_class_major);
   }
 }
 
@@ -512,6 +521,7 @@ __global__ void __launch_bounds__(threads_for_logb(LOGB - LOGP), 1) deflate_kern
 // transforms (length b / 2^logp) must be 2^13 or 2^14 when logp > 0.
 int launch_contract(int log2b, int logp, int mode, const ContractArgs& args, cudaStream_t st);
 int launch_deflate(int log2b, int logp, const DeflateArgs& args, int B, cudaStream_t st);
-int launch_fft_split(int log2b, int logp, const float2* S, float2* FS, int B, cudaStream_t st);
+int launch_fft_split(int log2b, int logp, const float2* S, float2* FS, int B, cudaStream_t st,
+                     int class_major = 0);
 
 }  // namespace tsk
