@@ -1117,7 +1117,8 @@ def run_profile(args):
     'build'    -- 4 launches of the symmetric sketch build on the n = 400 tensor;
     'rtpm'     -- 2 full steps (hashes, build, Alg. 1), the first one a warm-up;
     'lda'      -- 2 spectral_lda steps on a D = 1e5 corpus (otherwise the LDA workload);
-    'cp'       -- asymmetric build + rfft, then 3 CP loss + adjoint evaluations (cfg of run_cp)."""
+    'cp'       -- asymmetric build + rfft, then 3 CP loss + adjoint evaluations (cfg of run_cp);
+    'm3'       -- 2 lda_whitened_m3 calls on a D = 1e5 corpus (V = 50000, k = 100)."""
     import torch
     import paper_1506_04448_gb300 as tsk
     dev = torch.device("cuda:0")
@@ -1145,6 +1146,21 @@ def run_profile(args):
         torch.cuda.synchronize(dev)
         tsk.check_status(dev)
         print("profile orderp done")
+        return
+    if args.profile == "m3":
+        import synth
+        lc = dict(LDA_CFG, D=100000)
+        V, k = lc["V"], lc["k"]
+        c = synth.lda_corpus(V, k, lc["D"], lc["seed"], alpha=lc["alpha"], beta=lc["beta"],
+                             mean_len=lc["mean_len"])
+        ip, idx, cnt = (torch.from_numpy(np.ascontiguousarray(c[x])).to(dev)
+                        for x in ("indptr", "idx", "cnt"))
+        W = torch.from_numpy((synth.gaussian_matrix(V, k, 4) / np.sqrt(V)).astype(np.float32)).to(dev)
+        for _ in range(2):
+            tsk.lda_whitened_m3(ip, idx, cnt, V, W, k * lc["alpha"])
+        torch.cuda.synchronize(dev)
+        tsk.check_status(dev)
+        print("profile m3 done")
         return
     if args.profile == "lda":
         import synth
@@ -1189,7 +1205,7 @@ def run_profile(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile", choices=["contract", "build", "rtpm", "lda", "cp", "orderp"],
+    ap.add_argument("--profile", choices=["contract", "build", "rtpm", "lda", "cp", "orderp", "m3"],
                     default=None)
     ap.add_argument("--workload", choices=["decompose", "batched", "lda", "cp", "e1", "order4"],
                     default="decompose")
