@@ -132,6 +132,23 @@ int sketch_tensor(tsk_ctx* ctx, const void* T, int in_dtype, int M, const int64_
                   const int32_t* h, const uint8_t* g, int B, int log2b,
                   void* S, int acc_dtype, int accumulate);
 
+/* Colliding sketches (M = 1) of the wedge entries i <= j <= k of a symmetric n x n x n tensor
+ * whose first index i lies in [plane_begin, plane_end): the part of sketch_tensor's sum over
+ * those planes.  Sketches are linear in the tensor (Sec. 3.1), so the sum of the sketches of a
+ * partition of 0..n-1 into plane ranges, built on different devices and added (e.g. by an
+ * all-reduce), is the sketch of the whole tensor: exactly with TSK_CI64, up to float rounding
+ * with TSK_C64 (each part is rounded on its own grid, set by max|T| over its planes).
+ * T: planes plane_begin .. plane_end - 1 only, [plane_end - plane_begin][n][n] row-major, i.e.
+ *   the slice T[plane_begin:plane_end] of the full tensor (no other entries are read); may be
+ *   NULL when the range is empty.
+ * h, g: [B][n] hash tables as for sketch_tensor with M = 1.  Other arguments, workspace use,
+ * status reporting and limits as for sketch_tensor with M = 1.  An empty range writes zeros
+ * (accumulate = 0) or leaves S unchanged.
+ * Returns TSK_EINVAL unless 0 <= plane_begin <= plane_end <= n. */
+int sketch_tensor_planes(tsk_ctx* ctx, const void* T, int in_dtype, int n, int plane_begin,
+                         int plane_end, const int32_t* h, const uint8_t* g, int B, int log2b,
+                         void* S, int acc_dtype, int accumulate);
+
 /* Batched length-b DFT of B complex float vectors (S_in, S_out: [B][b] TSK_C64; may alias).
  * inverse = 0: unnormalised forward transform; 1: inverse transform including 1/b. */
 int sketch_fft(tsk_ctx* ctx, const float* S_in, float* S_out, int B, int log2b, int inverse);

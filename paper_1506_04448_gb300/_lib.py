@@ -31,6 +31,7 @@ SIGNATURES = {
     "tsk_peak_work": (_I, [_P, _I, _I, ctypes.POINTER(_D)]),
     "cs_hashes": (_I, [_P, _U64, _I, _I, _I, _P, _P, _P]),
     "sketch_tensor": (_I, [_P, _P, _I, _I, _P, _P, _P, _I, _I, _P, _I, _I]),
+    "sketch_tensor_planes": (_I, [_P, _P, _I, _I, _I, _I, _P, _P, _I, _I, _P, _I, _I]),
     "sketch_fft": (_I, [_P, _P, _P, _I, _I, _I]),
     "sketch_rank1": (_I, [_P, _I64, _P, _P, _P, _P, _I, _P, _P, _P, _I, _I, _I, _P, _I]),
     "contract_iuu": (_I, [_P, _P, _P, _P, _P, _I, _I, _P, _I, _I64, _P, _P]),

@@ -156,6 +156,77 @@ def sketch_tensor(T: torch.Tensor, h: torch.Tensor, g: torch.Tensor, log2b: int,
     return S
 
 
+_ACC_CODES = {"c64": (torch.complex64, _lib.TSK_C64), "c128": (torch.complex128, _lib.TSK_C128),
+              "ci64": (torch.int64, _lib.TSK_CI64)}
+
+
+def sketch_tensor_planes(T_planes: torch.Tensor, h: torch.Tensor, g: torch.Tensor, log2b: int,
+                         plane_begin: int, *, S: torch.Tensor | None = None,
+                         accumulate: bool = False, acc: str = "c64"):
+    """Colliding sketches (Eq. 7) of the wedge entries i <= j <= k whose first index lies in
+    [plane_begin, plane_begin + T_planes.shape[0]) of a symmetric n^3 tensor, from the slice
+    T_planes = T[plane_begin:plane_end] ([planes][n][n]).  By linearity (Sec. 3.1) the sketches
+    of a partition of the planes add up to the sketch of T."""
+    device = T_planes.device
+    if T_planes.dtype not in _IN_DTYPES:
+        raise TypeError("T_planes must be float32, float64 or int32")
+    _need(T_planes, "T_planes", T_planes.dtype, device)
+    h, g = _hashes_shape(h, g)
+    _need(h, "h", torch.int32, device)
+    _need(g, "g", torch.uint8, device)
+    B, M, n = h.shape
+    if M != 1:
+        raise ValueError("plane ranges apply to the colliding sketch (h.shape[1] == 1)")
+    if T_planes.dim() != 3 or T_planes.shape[1] != n or T_planes.shape[2] != n:
+        raise ValueError("T_planes must be [planes][n][n] with n = h.shape[-1]")
+    plane_end = plane_begin + T_planes.shape[0]
+    if plane_begin < 0 or plane_end > n:
+        raise ValueError("planes out of range")
+    if acc not in _ACC_CODES:
+        raise ValueError("acc must be 'c64', 'c128' or 'ci64'")
+    dt, code = _ACC_CODES[acc]
+    b = 1 << log2b
+    shape = (B, b, 2) if acc == "ci64" else (B, b)
+    if S is None:
+        if accumulate:
+            raise ValueError("accumulate=True needs S")
+        S = torch.empty(shape, dtype=dt, device=device)
+    _need(S, "S", dt, device, shape)
+    rc = _lib.load().sketch_tensor_planes(_ctx(device), _ptr(T_planes), _IN_DTYPES[T_planes.dtype],
+                                          n, plane_begin, plane_end, _ptr(h), _ptr(g), B, log2b,
+                                          _ptr(S), code, int(accumulate))
+    _lib.check("sketch_tensor_planes", rc)
+    return S
+
+
+def plane_ranges(n: int, parts: int) -> list[tuple[int, int]]:
+    """Split the planes 0..n-1 of the wedge into `parts` consecutive ranges with about equal
+    numbers of wedge entries (plane i holds (n - i)(n - i + 1) / 2 of them).  Host-side only."""
+    if parts < 1 or n < 0:
+        raise ValueError("need parts >= 1 and n >= 0")
+    sizes = [(n - i) * (n - i + 1) // 2 for i in range(n)]
+    total = sum(sizes)
+    cuts, acc, r = [0], 0, 1
+    for i, w in enumerate(sizes):
+        acc += w
+        while r < parts and acc * parts >= total * r:
+            cuts.append(i + 1)
+            r += 1
+    while len(cuts) < parts:
+        cuts.append(n)
+    cuts.append(n)
+    return [(cuts[r], cuts[r + 1]) for r in range(parts)]
+
+
+def allreduce_sketches(S: torch.Tensor, group=None) -> torch.Tensor:
+    """Sum partial sketches across the ranks of a torch.distributed process group, in place
+    (Sec. 3.1: the sketch of a sum of tensors is the sum of their sketches)."""
+    import torch.distributed as dist
+    buf = torch.view_as_real(S) if S.is_complex() else S
+    dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
+    return S
+
+
 def sketch_fft(S: torch.Tensor, inverse: bool = False, out: torch.Tensor | None = None):
     """Batched DFT of the rows of a complex64 [B][b] tensor (inverse includes 1/b)."""
     device = S.device

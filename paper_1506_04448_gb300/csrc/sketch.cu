@@ -42,7 +42,8 @@ struct SymSketchArgs {
   const int32_t* h;   // [B][n]
   const uint8_t* g;   // [B][n]
   int log2b;
-  long long W;        // wedge size n(n+1)(n+2)/6
+  long long W;        // wedge entries to build (those of the planes asked for)
+  long long E0;       // wedge position of the first of them
   int nslab;
   void* S;            // [B][b][2] accumulator type
   int log2r;          // the buckets are split into 2^log2r ranges, one block per range
@@ -76,8 +77,8 @@ __global__ void __launch_bounds__(1024, 1) sketch_sym_kernel(SymSketchArgs a) {
   // this block owns the wedge rows (i <= j) whose first entry lies in [e0, e1)
   const TIn* T = static_cast<const TIn*>(a.T);
   const long long per_slab = (a.W + a.nslab - 1) / a.nslab;
-  const long long e0 = (long long)blockIdx.y * per_slab;
-  const long long e1 = min(a.W, e0 + per_slab);
+  const long long e0 = a.E0 + (long long)blockIdx.y * per_slab;
+  const long long e1 = min(a.E0 + a.W, e0 + per_slab);
   if (tid < 2) {
     // first row whose start is >= e (e = e0 for thread 0, e1 for thread 1)
     const long long e = tid == 0 ? e0 : e1;
@@ -191,35 +192,38 @@ constexpr int kMaxTileCols = 256;   // nc = ceil(n / 32) for n <= 8192
 // max |T_ijk| over the wedge i <= j <= k as float bits, into *maxbits (zeroed by the caller).
 // Warps take the wedge's tiles (all planes) and load a tile's up to 32 rows at once.
 template <typename TIn>
-__global__ void __launch_bounds__(256) wedge_absmax_kernel(const TIn* __restrict__ T, int n,
-                                                           unsigned* maxbits) {
+__global__ void __launch_bounds__(256) wedge_absmax_kernel(const TIn* __restrict__ T, int n, int i0,
+                                                           int i1, unsigned* maxbits) {
+  // planes [i0, i1): row blocks rb >= i0 / 32, each with planes i0 .. min(i1, 32 rb + 32) - 1
   __shared__ unsigned smax;
-  __shared__ int pre[kMaxTileCols + 1];   // tiles before row block rb
+  __shared__ int pre[kMaxTileCols + 1];   // tiles before row block rb0 + q
   const int nc = (n + 31) >> 5;
+  const int rb0 = i0 >> 5, nrb = nc - rb0;
   if (threadIdx.x == 0) {
     smax = 0u;
     int acc = 0;
-    for (int rb = 0; rb < nc; ++rb) {
-      pre[rb] = acc;
-      acc += min(n, 32 * rb + 32) * (nc - rb);
+    for (int q = 0; q < nrb; ++q) {
+      pre[q] = acc;
+      const int rb = rb0 + q;
+      acc += max(0, min(i1, 32 * rb + 32) - i0) * (nc - rb);
     }
-    pre[nc] = acc;
+    pre[nrb] = acc;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   uint32_t mb = 0u;
-  for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < pre[nc]; it += nwarps) {
-    int lo = 0, hi = nc - 1;
+  for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < pre[nrb]; it += nwarps) {
+    int lo = 0, hi = nrb - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (pre[mid] <= it) lo = mid; else hi = mid - 1;
     }
-    const int rb = lo;
-    const int nir = min(n, 32 * rb + 32);
-    const int local = it - pre[rb];
+    const int rb = rb0 + lo;
+    const int nir = min(i1, 32 * rb + 32) - i0;
+    const int local = it - pre[lo];
     const int c = rb + local / nir;
-    const int i = local % nir;
+    const int i = i0 + local % nir;
     const int jlo = max(i, 32 * rb), jhi = min(32 * rb + 32, n);
     const int k = 32 * c + lane;
     const int jlim = k >= n ? -1 : (rb == c ? min(k, jhi - 1) : jhi - 1);
@@ -638,8 +642,8 @@ static int launch_sym_fix_t(const SymFixArgs& a, int groups, size_t smem, tsk_ct
 }
 
 template <typename TIn>
-static int launch_sym_fix(const void* T, int n, const int32_t* h, const uint8_t* g, int B,
-                          int log2b, void* S, int accumulate, tsk_ctx* ctx) {
+static int launch_sym_fix(const void* T, int n, int p0, int p1, const int32_t* h, const uint8_t* g,
+                          int B, int log2b, void* S, int accumulate, tsk_ctx* ctx) {
   const size_t b = (size_t)1 << log2b;
   const size_t smax = (size_t)ctx->max_smem_optin - 2048;   // the kernel's static tables
   auto smem_for = [&](int sk, int lr) {
@@ -667,13 +671,16 @@ static int launch_sym_fix(const void* T, int n, const int32_t* h, const uint8_t*
   a.log2b = log2b;
   a.log2r = log2r;
   // one wave of 1024-thread blocks (one per SM); slabs are plane ranges of about equal wedge
-  // size (plane i holds (n - i)(n - i + 1) / 2 entries), none below ~16k entries
-  const long long W = (long long)n * (n + 1) * (n + 2) / 6;
+  // size (plane i holds (n - i)(n - i + 1) / 2 entries), none below ~16k entries; only the
+  // planes [p0, p1) are built
+  auto tet = [](long long x) { return x * (x + 1) * (x + 2) / 6; };
+  const long long W = tet(n - p0) - tet(n - p1);
   long long nslab = (long long)ctx->num_sms / ((long long)groups * R);
   if (nslab < 1) nslab = 1;
   const long long cap = (W + 16383) / 16384;
   if (nslab > cap) nslab = cap;
-  if (nslab > n) nslab = n;
+  if (nslab > p1 - p0) nslab = p1 - p0;
+  if (nslab < 1) nslab = 1;
   if (nslab > kMaxFixSlabs) nslab = kMaxFixSlabs;
   a.nslab = (int)nslab;
   {
@@ -689,17 +696,17 @@ static int launch_sym_fix(const void* T, int n, const int32_t* h, const uint8_t*
       return cost;
     };
     long long total = 0;
-    for (int i = 0; i < n; ++i) total += plane_cost(i);
-    a.plane0[0] = 0;
-    int i = 0, s = 1;
+    for (int i = p0; i < p1; ++i) total += plane_cost(i);
+    a.plane0[0] = p0;
+    int i = p0, s = 1;
     long long acc = 0;
-    while (s < a.nslab && i < n) {
+    while (s < a.nslab && i < p1) {
       acc += plane_cost(i++);
       while (s < a.nslab && acc * a.nslab >= total * s) a.plane0[s++] = i;
     }
-    while (s < a.nslab) a.plane0[s++] = n;
-    a.plane0[a.nslab] = n;
-    for (int q = 1; q < a.nslab; ++q)   // keep every slab non-empty (nslab <= n)
+    while (s < a.nslab) a.plane0[s++] = p1;
+    a.plane0[a.nslab] = p1;
+    for (int q = 1; q < a.nslab; ++q)   // keep every slab non-empty (nslab <= p1 - p0)
       if (a.plane0[q] <= a.plane0[q - 1]) a.plane0[q] = a.plane0[q - 1] + 1;
     for (int q = a.nslab - 1; q >= 1; --q)
       if (a.plane0[q] >= a.plane0[q + 1]) a.plane0[q] = a.plane0[q + 1] - 1;
@@ -715,7 +722,7 @@ static int launch_sym_fix(const void* T, int n, const int32_t* h, const uint8_t*
   a.maxbits = maxbits;
   TSK_CUDA(cudaMemsetAsync(ctx->ws, 0, head, ctx->stream));
   wedge_absmax_kernel<TIn><<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(static_cast<const TIn*>(T), n,
-                                                                    maxbits);
+                                                                    p0, p1, maxbits);
   TSK_CHECK_LAUNCH();
   if constexpr (std::is_same<TIn, float>::value) {
     if (SK == 4) rc = launch_sym_fix_t<TIn, 4, false>(a, groups, smem, ctx);
@@ -917,6 +924,33 @@ static int launch_rank1(int log2b, const Rank1Args& a, int B, cudaStream_t st) {
 
 using namespace tsk;
 
+// colliding sketches of the wedge entries whose first index lies in [p0, p1) (arguments checked
+// by the callers)
+static int sketch_sym_planes(tsk_ctx* ctx, const void* T, int in_dtype, int n, int p0, int p1,
+                             const int32_t* h, const uint8_t* g, int B, int log2b, void* S,
+                             int acc_dtype, int accumulate) {
+  if (p1 > p0 && log2b > 16) return TSK_EUNSUPPORTED;
+  const size_t b = (size_t)1 << log2b;
+  if (acc_dtype == TSK_C64 && p1 > p0) {
+    // complex-float sketches: exact int32 accumulation (writes or adds S itself)
+    if (in_dtype == TSK_F32) return launch_sym_fix<float>(T, n, p0, p1, h, g, B, log2b, S, accumulate, ctx);
+    if (in_dtype == TSK_F64) return launch_sym_fix<double>(T, n, p0, p1, h, g, B, log2b, S, accumulate, ctx);
+    return launch_sym_fix<int32_t>(T, n, p0, p1, h, g, B, log2b, S, accumulate, ctx);
+  }
+  const size_t elem = acc_dtype == TSK_C64 ? sizeof(float) : 8;
+  if (!accumulate) TSK_CUDA(cudaMemsetAsync(S, 0, (size_t)B * b * 2 * elem, ctx->stream));
+  if (p1 <= p0) return TSK_OK;
+  auto tet = [](long long x) { return x * (x + 1) * (x + 2) / 6; };
+  const long long E0 = tet(n) - tet(n - p0);
+  const long long W = tet(n - p0) - tet(n - p1);
+  SymSketchArgs a{T, n, h, g, log2b, W, E0, 1, S, 0};
+  if (acc_dtype == TSK_C128) {
+    if (in_dtype == TSK_F32) return launch_sym<float, double, 2>(a, B, ctx);
+    return launch_sym<double, double, 2>(a, B, ctx);
+  }
+  return launch_sym<int32_t, long long, 2>(a, B, ctx);
+}
+
 extern "C" int sketch_tensor(tsk_ctx* ctx, const void* T, int in_dtype, int M,
                              const int64_t* dims_host, const int32_t* h, const uint8_t* g, int B,
                              int log2b, void* S, int acc_dtype, int accumulate) {
@@ -930,26 +964,11 @@ extern "C" int sketch_tensor(tsk_ctx* ctx, const void* T, int in_dtype, int M,
     if (dims_host[j] < 0 || dims_host[j] > 8192) return dims_host[j] < 0 ? TSK_EINVAL : TSK_EUNSUPPORTED;
   const size_t b = (size_t)1 << log2b;
   const size_t elem = acc_dtype == TSK_C64 ? sizeof(float) : 8;
-  if (M == 1 && acc_dtype == TSK_C64 && dims_host[0] > 0) {
-    // complex-float colliding sketches: exact int32 accumulation (writes or adds S itself)
-    const int n = (int)dims_host[0];
-    if (log2b > 16) return TSK_EUNSUPPORTED;
-    if (in_dtype == TSK_F32) return launch_sym_fix<float>(T, n, h, g, B, log2b, S, accumulate, ctx);
-    if (in_dtype == TSK_F64) return launch_sym_fix<double>(T, n, h, g, B, log2b, S, accumulate, ctx);
-    return launch_sym_fix<int32_t>(T, n, h, g, B, log2b, S, accumulate, ctx);
-  }
-  if (!accumulate) TSK_CUDA(cudaMemsetAsync(S, 0, (size_t)B * b * 2 * elem, ctx->stream));
   if (M == 1) {
     const int n = (int)dims_host[0];
-    if (n == 0) return TSK_OK;
-    if (log2b > 16) return TSK_EUNSUPPORTED;
-    SymSketchArgs a{T, n, h, g, log2b, (long long)n * (n + 1) * (n + 2) / 6, 1, S, 0};
-    if (acc_dtype == TSK_C128) {
-      if (in_dtype == TSK_F32) return launch_sym<float, double, 2>(a, B, ctx);
-      return launch_sym<double, double, 2>(a, B, ctx);
-    }
-    return launch_sym<int32_t, long long, 2>(a, B, ctx);
+    return sketch_sym_planes(ctx, T, in_dtype, n, 0, n, h, g, B, log2b, S, acc_dtype, accumulate);
   }
+  if (!accumulate) TSK_CUDA(cudaMemsetAsync(S, 0, (size_t)B * b * 2 * elem, ctx->stream));
   const int n1 = (int)dims_host[0], n2 = (int)dims_host[1], n3 = (int)dims_host[2];
   if (n1 == 0 || n2 == 0 || n3 == 0) return TSK_OK;
   const int nmax = n1 > n2 ? (n1 > n3 ? n1 : n3) : (n2 > n3 ? n2 : n3);
@@ -966,6 +985,30 @@ extern "C" int sketch_tensor(tsk_ctx* ctx, const void* T, int in_dtype, int M,
     return launch_asym<double, double>(a, B, ctx);
   }
   return launch_asym<int32_t, long long>(a, B, ctx);
+}
+
+extern "C" int sketch_tensor_planes(tsk_ctx* ctx, const void* T, int in_dtype, int n,
+                                    int plane_begin, int plane_end, const int32_t* h,
+                                    const uint8_t* g, int B, int log2b, void* S, int acc_dtype,
+                                    int accumulate) {
+  if (!ctx || (!T && plane_end > plane_begin) || !h || !g || !S) return TSK_EINVAL;
+  if (B < 1 || log2b < 1 || log2b > 24 || n < 0) return TSK_EINVAL;
+  if (plane_begin < 0 || plane_end < plane_begin || plane_end > n) return TSK_EINVAL;
+  if (in_dtype != TSK_F32 && in_dtype != TSK_F64 && in_dtype != TSK_I32) return TSK_EINVAL;
+  if (acc_dtype != TSK_C64 && acc_dtype != TSK_C128 && acc_dtype != TSK_CI64) return TSK_EINVAL;
+  if (acc_dtype == TSK_CI64 && in_dtype != TSK_I32) return TSK_EINVAL;
+  if (acc_dtype == TSK_C128 && in_dtype == TSK_I32) return TSK_EINVAL;
+  if (n > 8192) return TSK_EUNSUPPORTED;
+  // the kernels address plane i at (i n) n entries from the tensor's origin; T starts at plane
+  // plane_begin, so the origin is moved back by that many planes (only planes >= plane_begin
+  // are read)
+  const size_t esz = in_dtype == TSK_F64 ? 8 : 4;
+  const void* T0 = plane_end > plane_begin
+                       ? reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(T) -
+                                                       (uintptr_t)plane_begin * n * n * esz)
+                       : nullptr;
+  return sketch_sym_planes(ctx, T0, in_dtype, n, plane_begin, plane_end, h, g, B, log2b, S,
+                           acc_dtype, accumulate);
 }
 
 extern "C" int sketch_fft(tsk_ctx* ctx, const float* S_in, float* S_out, int B, int log2b,
