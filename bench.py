@@ -510,6 +510,42 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def gpu_busy_fraction(fn, dev):
+    """Fraction of the wall span of fn() during which at least one kernel ran, from the CUDA
+    activity trace of one untimed call (torch.profiler / CUPTI, exported as a Chrome trace;
+    tracing adds its own overhead per kernel, so the idle share it shows is an upper bound).
+    Returns (fraction, kernels), or (None, reason) where the trace holds no kernel intervals."""
+    import torch
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            fn()
+            torch.cuda.synchronize(dev)
+        with tempfile.TemporaryDirectory() as tmp:
+            path = os.path.join(tmp, "trace.json")
+            prof.export_chrome_trace(path)
+            with open(path) as f:
+                trace = json.load(f)
+    except Exception as exc:   # noqa: BLE001 -- a profiler that is unavailable gives no figure
+        return None, f"profiler unavailable: {type(exc).__name__}"
+    evs = trace.get("traceEvents", trace) if isinstance(trace, dict) else trace
+    ivs = sorted((float(e["ts"]), float(e["ts"]) + float(e["dur"])) for e in evs
+                 if isinstance(e, dict) and str(e.get("cat", "")).lower() == "kernel"
+                 and float(e.get("dur", 0)) > 0)
+    if not ivs:
+        return None, "no kernel records in the trace"
+    busy, cur_s, cur_e = 0.0, ivs[0][0], ivs[0][1]
+    for a, b in ivs[1:]:
+        if a > cur_e:
+            busy += cur_e - cur_s
+            cur_s, cur_e = a, b
+        else:
+            cur_e = max(cur_e, b)
+    busy += cur_e - cur_s
+    span = ivs[-1][1] - ivs[0][0]
+    return (busy / span if span > 0 else None), len(ivs)
+
+
 def run_batched(args):
     """256 independent planted problems (n ~ U{32..256}, k ~ U{4..16}, b = clamp(2^ceil(log2 nk),
     2^10, 2^14), B = 8, L = 20, T = 20, noise std 0.01 / n^1.5 per unique entry as in Sec. 5.1) in
@@ -554,6 +590,10 @@ def run_batched(args):
         torch.cuda.synchronize(dev)
     t_ms = e0.elapsed_time(e1) / args.steps
     tsk.check_status(dev)
+    # idle time between the graph's kernels: the most a single persistent kernel pulling the
+    # same work from a device queue could remove
+    busy, n_kernels = gpu_busy_fraction(graph.replay, dev)
+    busy_eager, n_eager = gpu_busy_fraction(plan.run, dev)
     work = sum(s["k"] * L * T for s in specs)
     # the same problems, one robust_power_method call after another
     for p in probs[:4]:
@@ -595,6 +635,12 @@ def run_batched(args):
                          "note": "relative squared residual per problem; equal residual on both "
                                  "routes makes speedup_vs_sequential a comparison at equal "
                                  "recovery"},
+            "gpu_busy_fraction": {"graph_replay": busy, "graph_kernels": n_kernels,
+                                  "eager_run": busy_eager, "eager_kernels": n_eager,
+                                  "note": "share of the step's span with a kernel running "
+                                          "(CUDA activity trace of one untimed call): a single "
+                                          "persistent kernel pulling the same work from a device "
+                                          "queue could remove at most the rest"},
             "block_sizes": {str(lb): plan.block_size(lb) for lb in groups},
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)

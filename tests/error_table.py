@@ -218,21 +218,36 @@ def report_phase(path):
     h1, g1 = h1[:, 0], g1[:, 0]
     S = z["e1_S"].astype(np.complex128)
     U1 = synth.gaussian_inits(e["k"], e["L"], e["n"], e["seed"] + 3).astype(np.float32).astype(np.float64)
-    e_v = e_l = 0.0
+    e_v = e_l = e_lv = 0.0
+    moving = []
     for r in range(e["k"]):
         u = U1[r, int(z["e1_tau"][r])]
         u = u / np.linalg.norm(u)
         for _ in range(e["T"]):
             u, _ = O.power_step_sketched(S, u, h1, g1, b1, "fft")
+        u_next, _ = O.power_step_sketched(S, u, h1, g1, b1, "fft")
+        step = float(np.linalg.norm(u_next - u))
+        vg = z["e1_V"][r].astype(np.float64)
         lw, _ = O.eigenvalue_sketched(S, u, h1, g1, b1, "fft")
-        e_v = max(e_v, float(np.linalg.norm(z["e1_V"][r] - u)))
-        e_l = max(e_l, abs(float(z["e1_lam"][r]) - lw) / abs(lw))
-        S = O.deflate_sketches(S, float(z["e1_lam"][r]), z["e1_V"][r].astype(np.float64), h1, g1,
-                               b1, "fft")
-    rows.append(("n = 1000 grid cell (B = 20, b = 2^14): components after T = 30 updates from "
-                 "the same start, 10 rounds", "max ||v_gpu - v_oracle||", f"{e_v:.2e}", "—"))
-    rows.append(("n = 1000 grid cell: eigenvalues, oracle run end to end",
+        lv, _ = O.eigenvalue_sketched(S, vg, h1, g1, b1, "fft")
+        e_lv = max(e_lv, abs(float(z["e1_lam"][r]) - lv) / abs(lv))
+        if step < 1e-8:      # the oracle's iteration has converged from this start
+            e_v = max(e_v, float(np.linalg.norm(vg - u)))
+            e_l = max(e_l, abs(float(z["e1_lam"][r]) - lw) / abs(lw))
+        else:
+            moving.append(f"round {r}: oracle still moving by {step:.1e}, "
+                          f"||v_gpu - v_oracle|| = {np.linalg.norm(vg - u):.1e}")
+        S = O.deflate_sketches(S, float(z["e1_lam"][r]), vg, h1, g1, b1, "fft")
+    conv = e["k"] - len(moving)
+    rows.append((f"n = 1000 grid cell (B = 20, b = 2^14): components after T = 30 updates from "
+                 f"the same start, the {conv} of 10 rounds whose oracle iteration has converged",
+                 "max ||v_gpu - v_oracle||", f"{e_v:.2e}", "—"))
+    rows.append(("n = 1000 grid cell: eigenvalues of those rounds, oracle run end to end",
                  "max |err| / |lambda|", f"{e_l:.2e}", "—"))
+    rows.append(("n = 1000 grid cell: eigenvalue at the device's component, all 10 rounds",
+                 "max |lambda_gpu - lambda_oracle(v_gpu)| / |lambda|", f"{e_lv:.2e}", "1e-4"))
+    rows.append(("n = 1000 grid cell: rounds still moving after T = 30 (no fixed point to "
+                 "compare)", "oracle's last step; distance", "; ".join(moving) or "none", "—"))
     rows.append(("n = 1000 grid cell: deflated sketches after 10 rounds", "rel 2-norm",
                  f"{rel2(z['e1_S_deflated'].astype(np.complex128), S):.2e}", "1e-4"))
     # spectral LDA
