@@ -216,8 +216,26 @@ __global__ void m2_finish_kernel(const float* Yacc, const float* X, const float*
 }
 
 // ------------------------------------------------------------------ small dense FP64 algebra
-// Partial Gram matrices part[blk][a][b] = sum over the block's rows of X[r][a] Y[r][b], a, b < c.
-// Each thread owns a 4 x 4 tile; blockIdx.y selects a group of 256 tiles.
+// Compensated FP32 dot products (the Dot2 scheme of Ogita, Rump and Oishi, "Accurate sum and
+// dot product", SIAM J. Sci. Comput. 26, 2005): each product x y is split exactly into p + e
+// with an FMA, p is added to the running sum s by Knuth's TwoSum, and the two rounding errors
+// are summed in c.  s + c carries the sum as accurately as FP64 accumulation of the exact
+// products to within a factor of the condition of the sum, at about ten FP32 operations per
+// term against one FP64 FMA at this part's 1/64 FP64 rate.  Every operation is an explicit
+// round-to-nearest intrinsic, so that no multiply-add is contracted into an FMA.
+__device__ __forceinline__ void dot2_acc(float x, float y, float& s, float& c) {
+  const float p = __fmul_rn(x, y);
+  const float e = __fmaf_rn(x, y, -p);
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(q, e));
+}
+
+// Partial Gram matrices part[blk][a][b] = sum over the block's rows of X[r][a] Y[r][b], a, b < c,
+// accumulated with dot2_acc and written in FP64.  Each thread owns a 4 x 4 tile; blockIdx.y
+// selects a group of 256 tiles.
 constexpr int kGramRows = 32;
 __global__ void __launch_bounds__(256) gram_partial_kernel(const float* X, int ldx, const float* Y,
                                                             int ldy, int64_t rows, int c,
@@ -228,7 +246,7 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const float* X, int l
   const int tile = blockIdx.y * 256 + threadIdx.x;
   const bool active = tile < c4 * c4;
   const int ta = active ? tile / c4 : 0, tb = active ? tile % c4 : 0;
-  double acc[4][4] = {};
+  float accs[4][4] = {}, accc[4][4] = {};
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
   const int64_t r1 = min64(rows, r0 + rows_per_block);
   for (int64_t base = r0; base < r1; base += kGramRows) {
@@ -245,12 +263,12 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const float* X, int l
       for (int r = 0; r < nr; ++r) {
         const float4 xa = *reinterpret_cast<const float4*>(&xs[r][4 * ta]);
         const float4 yb = *reinterpret_cast<const float4*>(&ys[r][4 * tb]);
-        const double xv[4] = {xa.x, xa.y, xa.z, xa.w};
-        const double yv[4] = {yb.x, yb.y, yb.z, yb.w};
+        const float xv[4] = {xa.x, xa.y, xa.z, xa.w};
+        const float yv[4] = {yb.x, yb.y, yb.z, yb.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(xv[i], yv[j], acc[i][j]);
+          for (int j = 0; j < 4; ++j) dot2_acc(xv[i], yv[j], accs[i][j], accc[i][j]);
       }
     }
   }
@@ -261,7 +279,7 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const float* X, int l
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int a = 4 * ta + i, b = 4 * tb + j;
-      if (a < c && b < c) out[a * c + b] = acc[i][j];
+      if (a < c && b < c) out[a * c + b] = (double)accs[i][j] + (double)accc[i][j];
     }
 }
 
@@ -350,14 +368,24 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(const double* G, int c, 
   }
 }
 
-// out = Y M with Y [rows][c] (ld ldy, float) and M [c][cout] (FP64), accumulated in FP64; one
-// warp per row.  transposed_out = 1 stores out[j][row] (ld ldo) instead of out[row][j].  In
-// place (out == Y) is safe: each warp reads its whole row before writing it.
+// out = Y M with Y [rows][c] (ld ldy, float) and M [c][cout] (FP64); one warp per row.  M is
+// held in shared memory as M_hi + M_lo (float, M_lo = M - M_hi rounded), and each output sums
+// y M_hi with dot2_acc and y M_lo plainly into the compensation term, which keeps the
+// cancellation of an ill-conditioned first orthogonalisation pass (large M, orthonormal result)
+// to FP32 rounding of the result.  transposed_out = 1 stores out[j][row] (ld ldo) instead of
+// out[row][j].  In place (out == Y) is safe: each warp reads its whole row before writing it.
 __global__ void __launch_bounds__(256) rmul_kernel(const float* Y, int ldy, int64_t rows, int c,
                                                     const double* M, int cout, float* out, int ldo,
                                                     int transposed_out) {
-  extern __shared__ double Ms[];
-  for (int e = threadIdx.x; e < c * cout; e += blockDim.x) Ms[e] = M[e];
+  extern __shared__ float Mhl[];
+  float* Mhi = Mhl;
+  float* Mlo = Mhl + c * cout;
+  for (int e = threadIdx.x; e < c * cout; e += blockDim.x) {
+    const double m = M[e];
+    const float hi = __double2float_rn(m);
+    Mhi[e] = hi;
+    Mlo[e] = __double2float_rn(m - (double)hi);
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t warp = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
@@ -369,17 +397,20 @@ __global__ void __launch_bounds__(256) rmul_kernel(const float* Y, int ldy, int6
       const int a = lane + 32 * t;
       yr[t] = a < c ? Y[r * ldy + a] : 0.f;
     }
-    double acc[kMaxWhitenCols / 32] = {};
+    float accs[kMaxWhitenCols / 32] = {}, accc[kMaxWhitenCols / 32] = {};
 #pragma unroll
     for (int t = 0; t < kMaxWhitenCols / 32; ++t) {
       for (int l = 0; l < 32; ++l) {
         const int a = 32 * t + l;
         if (a >= c) break;
-        const double ya = (double)__shfl_sync(0xffffffffu, yr[t], l);
+        const float ya = __shfl_sync(0xffffffffu, yr[t], l);
 #pragma unroll
         for (int u = 0; u < kMaxWhitenCols / 32; ++u) {
           const int j = lane + 32 * u;
-          if (j < cout) acc[u] = fma(ya, Ms[a * cout + j], acc[u]);
+          if (j < cout) {
+            dot2_acc(ya, Mhi[a * cout + j], accs[u], accc[u]);
+            accc[u] = __fmaf_rn(ya, Mlo[a * cout + j], accc[u]);
+          }
         }
       }
     }
@@ -388,8 +419,9 @@ __global__ void __launch_bounds__(256) rmul_kernel(const float* Y, int ldy, int6
     for (int u = 0; u < kMaxWhitenCols / 32; ++u) {
       const int j = lane + 32 * u;
       if (j < cout) {
-        if (transposed_out) out[(int64_t)j * ldo + r] = (float)acc[u];
-        else out[r * ldo + j] = (float)acc[u];
+        const float v = __fadd_rn(accs[u], accc[u]);
+        if (transposed_out) out[(int64_t)j * ldo + r] = v;
+        else out[r * ldo + j] = v;
       }
     }
   }
@@ -918,8 +950,8 @@ int run_chol_inv(tsk_ctx* ctx, const double* G, int c, double shift_scale, doubl
 
 int run_rmul(tsk_ctx* ctx, const float* Y, int ldy, int64_t rows, int c, const double* M, int cout,
              float* out, int ldo, int transposed) {
-  const size_t smem = (size_t)c * cout * sizeof(double);
-  TSK_CUDA(tsk_smem_attr<rmul_kernel>((size_t)kMaxWhitenCols * kMaxWhitenCols * sizeof(double)));
+  const size_t smem = (size_t)c * cout * 2 * sizeof(float);
+  TSK_CUDA(tsk_smem_attr<rmul_kernel>((size_t)kMaxWhitenCols * kMaxWhitenCols * 2 * sizeof(float)));
   rmul_kernel<<<grid_for(ctx, rows), 256, smem, ctx->stream>>>(Y, ldy, rows, c, M, cout, out, ldo,
                                                                transposed);
   TSK_CHECK_LAUNCH();
