@@ -428,10 +428,15 @@ __global__ void __launch_bounds__(256) rmul_kernel(const float* Y, int ldy, int6
 }
 
 // Symmetric eigendecomposition of (Bm + Bm^T)/2 (c x c, FP64) by the cyclic Jacobi method with
-// the round-robin ordering: every round applies c/2 disjoint plane rotations at once (rows
-// first, then columns; disjoint pairs commute), a sweep is c-1 rounds (every pair once).  Stops
-// when the off-diagonal Frobenius norm is below 1e-15 of the whole norm, or after max_sweeps.
-// One block; A in shared memory; eigenvectors (columns of evec, global) accumulate the rotations.
+// the round-robin ordering: every round applies c/2 disjoint plane rotations at once (disjoint
+// pairs commute), a sweep is c-1 rounds (every pair once).  A round updates A <- J^T A J as 2 x 2
+// blocks: block (t1, t2) of pairs t1 <= t2 becomes R1^T X R2 (rows by pair t1's rotation, columns
+// by pair t2's), and its mirror is written as the transpose, so each element of the symmetric A
+// is computed once; the eigenvectors accumulate E <- E J.  A rotation whose off-diagonal element
+// is below 2^-54 of both diagonal elements (smaller than their rounding) is not applied: the
+// element is set to zero (Rutishauser's threshold rule), and blocks of two such pairs are
+// skipped.  Stops when the off-diagonal Frobenius norm is below 1e-15 of the whole norm, or after
+// max_sweeps.  One block; A in shared memory; eigenvectors in global memory (columns of evec).
 __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double* Bm, int c, int max_sweeps,
                                                            double* evec, double* evals) {
   extern __shared__ double sh[];
@@ -448,6 +453,7 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double* Bm, int 
   __syncthreads();
   const int n2 = c + (c & 1);          // even number of players (one dummy when c is odd)
   const int npair = n2 / 2;
+  const int nblk = npair * (npair + 1) / 2;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
@@ -468,8 +474,13 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double* Bm, int 
         double cs = 1.0, sn = 0.0;
         if (q < c) {
           const double apq = A[p * ld + q];
-          if (apq != 0.0) {
-            const double tau = (A[q * ld + q] - A[p * ld + p]) / (2.0 * apq);
+          const double app = A[p * ld + p], aqq = A[q * ld + q];
+          const double tiny = 0x1p-54 * fmin(fabs(app), fabs(aqq));
+          if (fabs(apq) <= tiny) {
+            A[p * ld + q] = 0.0;           // below the diagonal's rounding: dropped
+            A[q * ld + p] = 0.0;
+          } else {
+            const double tau = (aqq - app) / (2.0 * apq);
             const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
             cs = 1.0 / sqrt(1.0 + tt * tt);
             sn = tt * cs;
@@ -481,24 +492,52 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double* Bm, int 
         rq[t] = q < c ? q : -1;
       }
       __syncthreads();
-      for (int e = threadIdx.x; e < npair * c; e += blockDim.x) {   // rows: A <- J^T A
-        const int t = e / c, j = e % c;
-        const int q = rq[t];
-        if (q < 0 || rs[t] == 0.0) continue;
-        const int p = rp[t];
-        const double a = A[p * ld + j], b = A[q * ld + j];
-        A[p * ld + j] = rc[t] * a - rs[t] * b;
-        A[q * ld + j] = rs[t] * a + rc[t] * b;
+      // A <- J^T A J by 2 x 2 blocks (t1 <= t2); a missing index (the dummy) is a 1-wide block
+      for (int e = threadIdx.x; e < nblk; e += blockDim.x) {
+        int t1 = 0, rem = e;
+        while (rem >= npair - t1) { rem -= npair - t1; ++t1; }
+        const int t2 = t1 + rem;
+        const double s1 = rs[t1], s2 = rs[t2];
+        if (s1 == 0.0 && s2 == 0.0) continue;
+        const double c1 = rc[t1], c2 = rc[t2];
+        const int p1 = rp[t1], q1 = rq[t1], p2 = rp[t2], q2 = rq[t2];
+        const double x00 = A[p1 * ld + p2];
+        const double x01 = q2 >= 0 ? A[p1 * ld + q2] : 0.0;
+        const double x10 = q1 >= 0 ? A[q1 * ld + p2] : 0.0;
+        const double x11 = (q1 >= 0 && q2 >= 0) ? A[q1 * ld + q2] : 0.0;
+        // rows by (c1, s1): row p1' = c1 row p1 - s1 row q1, row q1' = s1 row p1 + c1 row q1
+        const double y00 = c1 * x00 - s1 * x10, y01 = c1 * x01 - s1 * x11;
+        const double y10 = s1 * x00 + c1 * x10, y11 = s1 * x01 + c1 * x11;
+        // columns by (c2, s2)
+        const double z00 = c2 * y00 - s2 * y01, z01 = s2 * y00 + c2 * y01;
+        const double z10 = c2 * y10 - s2 * y11, z11 = s2 * y10 + c2 * y11;
+        if (t1 == t2) {
+          // the pair's own block: the rotation annihilates its off-diagonal element
+          A[p1 * ld + p1] = z00;
+          if (q1 >= 0) {
+            A[q1 * ld + q1] = z11;
+            A[p1 * ld + q1] = 0.0;
+            A[q1 * ld + p1] = 0.0;
+          }
+          continue;
+        }
+        A[p1 * ld + p2] = z00;
+        if (q2 >= 0) A[p1 * ld + q2] = z01;
+        if (q1 >= 0) A[q1 * ld + p2] = z10;
+        if (q1 >= 0 && q2 >= 0) A[q1 * ld + q2] = z11;
+        {
+          A[p2 * ld + p1] = z00;
+          if (q2 >= 0) A[q2 * ld + p1] = z01;
+          if (q1 >= 0) A[p2 * ld + q1] = z10;
+          if (q1 >= 0 && q2 >= 0) A[q2 * ld + q1] = z11;
+        }
       }
-      __syncthreads();
-      for (int e = threadIdx.x; e < npair * c; e += blockDim.x) {   // columns: A <- A J, E <- E J
+      // E <- E J (columns p, q of every row)
+      for (int e = threadIdx.x; e < npair * c; e += blockDim.x) {
         const int t = e / c, i = e % c;
         const int q = rq[t];
         if (q < 0 || rs[t] == 0.0) continue;
         const int p = rp[t];
-        const double a = A[i * ld + p], b = A[i * ld + q];
-        A[i * ld + p] = rc[t] * a - rs[t] * b;
-        A[i * ld + q] = rs[t] * a + rc[t] * b;
         const double ea = evec[i * c + p], eb = evec[i * c + q];
         evec[i * c + p] = rc[t] * ea - rs[t] * eb;
         evec[i * c + q] = rs[t] * ea + rc[t] * eb;
