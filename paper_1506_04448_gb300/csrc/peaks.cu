@@ -1,4 +1,4 @@
-// Micro-kernels that measure the on-chip roofs the contraction and build kernels are judged
+// Micro-kernels that measure the on-chip roofs the contraction and build kernels are measured
 // against: FP32 FMA issue rate, shared-memory load bandwidth, and the rate of random-bucket
 // int32 shared-memory atomics (the build's scatter).  The paper has no counterpart; the caller
 // times each launch with events on the context's stream and divides the work by the time.
