@@ -118,13 +118,14 @@ int cs_hashes(tsk_ctx* ctx, uint64_t seed, int B, int log2b, int M, const int64_
  *   zero imaginary part: S[m][t] = sum_{(h1+h2+h3) mod b = t} xi1 xi2 xi3 T_ijk.
  * in_dtype: TSK_F32 | TSK_F64 | TSK_I32.  acc_dtype: TSK_C64 (complex float result, any input),
  *   TSK_C128 (double accumulation, F64 input) or TSK_CI64 (exact int64, I32 input).
- * M = 1 with TSK_C64: every wedge entry is rounded once to the integer grid 2^(E-25), where 2^E
- *   is the smallest power of two above max|T| over the wedge, and the buckets are summed exactly
- *   in integers; the only other rounding is the final conversion to float.  The result does not
- *   depend on thread scheduling (two calls give identical bits).  A non-finite entry makes every
- *   value of S NaN and is reported by tsk_ctx_status() as TSK_ENONFINITE.  Uses context
- *   workspace of about (nslab + 1) * B * 2b * 4 bytes, nslab <= number of SMs / (B / sketches per
- *   block).
+ * TSK_C64 (M = 1 and M = 3): every entry read is rounded once to the integer grid 2^(E-25), where
+ *   2^E is the smallest power of two above max|T| over the entries read (the wedge for M = 1,
+ *   the whole tensor for M = 3), and the buckets are summed exactly in integers; the only other
+ *   rounding is the final conversion to float.  The result does not depend on thread scheduling
+ *   (two calls give identical bits).  A non-finite entry (or an FP64 entry beyond the float range)
+ *   makes every value of S NaN and is reported by tsk_ctx_status() as TSK_ENONFINITE.  Uses
+ *   context workspace of about (nslab + 1) * B * 2b * 4 bytes (M = 1) or (nslab + 1) * B * b * 4
+ *   bytes (M = 3), nslab <= the number of SMs.
  * S: [B][b] of acc_dtype.  accumulate = 0 overwrites S, 1 adds to it.
  * Limits: symmetric path log2b <= 16 (M = 1; above 2^14 the buckets are built in 2 or 4
  * ranges by separate blocks), asymmetric path log2b <= 15, n <= 8192. */

@@ -4,11 +4,11 @@
 //   E3[a][b][c] = sum_d w_d p_da p_db p_dc
 // is the product of X[(a,b)][d] = w_d p_da p_db (one row per pair a <= b) with P: a GEMM of
 // k (k + 1) / 2 rows, k columns and D as the contraction dimension.  It runs as tcgen05.mma
-// kind::tf32 with the FP32 operands split into TF32 hi + lo parts and three products per step
-// (hi hi + hi lo + lo hi), which keeps each product to about 2^-21 relative; the accumulator lives
-// in tensor memory.
+// kind::tf32 with the FP32 operands split into TF32 hi + lo parts, both rounded to nearest, and
+// three products per step (hi lo + lo hi first, then hi hi), which keeps each product to about
+// 2^-22 relative without a bias of one sign; the accumulator lives in tensor memory.
 //
-// One CTA (512 threads) takes 128 pairs and one contiguous range of documents, 32 documents per
+// One CTA (512 build threads and one MMA warp) takes 128 pairs and one contiguous range of documents, 32 documents per
 // step.  The step's rows of P arrive in shared memory by one bulk copy issued two steps ahead.
 // Every warp builds a 32-row x 8-document block of X (its lanes' pairs, in registers) and writes
 // it, split into TF32 hi and lo, to the step's A stage in tensor memory (rows = lanes); the warps
@@ -76,11 +76,15 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mbar) : "memory");
 }
 
-// x = hi + lo with hi the TF32 truncation of x (low 13 mantissa bits cleared); lo = x - hi is
-// exact in FP32 and below 2^-10 |x|, and the tensor cores' own truncation of lo to TF32 costs at
-// most 2^-20 |x|.
-__device__ __forceinline__ float tf32_hi(float x) {
-  return __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+// x rounded to TF32 (10 explicit mantissa bits), to nearest.  The split x = hi + lo uses
+// hi = tf32_rn(x) and lo = tf32_rn(x - hi): x - hi is exact in FP32 and at most 2^-11 |x|, and
+// rounding it costs at most 2^-22 |x|.  Both roundings are to nearest, so that their errors do
+// not add up with one sign over the many documents of a sum (truncation would: a bias of about
+// 2^-21 per product, which the cancellation between the moment's terms magnifies).
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
 }
 
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
@@ -98,6 +102,10 @@ __device__ __forceinline__ void tmem_st4(uint32_t taddr, const float* v) {
 }
 
 constexpr int kTcWarps = 16;   // build and merge warps; warp 16 issues the MMAs
+// Steps per accumulation run: a run's MMAs accumulate in one tensor-memory accumulator (the
+// tensor cores' FP32 additions are not rounded to nearest), which is then folded into the FP32
+// running sum with round-to-nearest.
+constexpr int kTcRun = 2;
 constexpr int kTcThreads = (kTcWarps + 1) * 32;
 constexpr int kTcColA = 384;   // A operand stages: stage s hi at 384 + 64 s, lo 32 columns on
 
@@ -184,7 +192,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) moments3_tc_kernel(Moments3TcAr
       for (int c = c0; c < c0 + qcols; c += 4) tmem_st4(tmem + lane_base + kTcColSum + c, z);
     asm volatile("tcgen05.wait::st.sync.aligned;");
   }
-  // add the accumulator of the step pair ending at local step j (finished) into the running sum
+  // add the accumulator of the run ending at local step j (finished) into the running sum
   // (FP32, round to nearest)
   auto merge = [&](long long j) -> bool {
     bool ok = !*(volatile int*)&s_abort &&
@@ -192,7 +200,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) moments3_tc_kernel(Moments3TcAr
     ok = __all_sync(0xffffffffu, ok);   // the tensor-memory accesses below are warp-wide
     if (!ok) return false;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t accol = (uint32_t)((j >> 1) & 1) * kTcColAcc1;
+    const uint32_t accol = (uint32_t)((j / kTcRun) & 1) * kTcColAcc1;
     // 16 columns at a time (qcols <= 32): the loads first (4 columns each), one wait, the stores
 #pragma unroll
     for (int h = 0; h < 32; h += 16) {
@@ -233,9 +241,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) moments3_tc_kernel(Moments3TcAr
   long long issued = 0;
   if (warp == kTcWarps) {
     // ---------------- MMA warp: step i's 12 MMAs once its operands are built, A from tensor
-    // memory, B from shared memory, into accumulator (i / 2) mod 2, from zero on even steps (a
-    // pair of steps, 24 MMAs, per accumulator: the tensor cores' FP32 accumulation is not
-    // rounded to nearest)
+    // memory, B from shared memory, into accumulator (i / kTcRun) mod 2, from zero at the start
+    // of each run of kTcRun steps
     if (lane == 0) {
       const uint32_t bbytes = (uint32_t)(N * kTcDocs * 4);
       for (long long i = 0; i < nsteps; ++i) {
@@ -245,15 +252,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) moments3_tc_kernel(Moments3TcAr
         if (!ok) { atomicExch(&s_abort, 1); break; }
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t bb = smem_u32(sm + stg * bstage);
-        const uint32_t dcol = tmem + (uint32_t)((i >> 1) & 1) * kTcColAcc1;
+        const uint32_t dcol = tmem + (uint32_t)((i / kTcRun) & 1) * kTcColAcc1;
         const uint32_t acol = tmem + kTcColA + 64u * stg;
+        // the small terms (hi lo, lo hi) first, then hi hi: the accumulator's FP32 additions are
+        // not rounded to nearest, and an addition costs up to one unit in the last place of the
+        // accumulator, so the adds made while it is still small cost little
 #pragma unroll
-        for (int ks = 0; ks < kTcDocs / 8; ++ks) {
+        for (int pass = 1; pass < 4; ++pass) {
 #pragma unroll
-          for (int pass = 0; pass < 3; ++pass) {
+          for (int ks = 0; ks < kTcDocs / 8; ++ks) {
             const uint32_t at = acol + (pass == 2 ? 32u : 0u) + 8u * ks;
             const uint64_t bd = smem_desc(bb + (pass == 1 ? bbytes : 0u) + ks * 256, 128, 1024);
-            const uint32_t acc = (ks == 0 && pass == 0 && (i & 1) == 0) ? 0u : 1u;
+            const uint32_t acc = (ks == 0 && pass == 1 && (i % kTcRun) == 0) ? 0u : 1u;
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}"
@@ -288,8 +298,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) moments3_tc_kernel(Moments3TcAr
       for (int j = 0; j < 8; ++j) {
         const int d = 8 * ch + j;
         const float x = (pa >= 0 && d < nv) ? w[j] * Ps[d * kp + pa] * Ps[d * kp + pb] : 0.f;
-        hi[j] = tf32_hi(x);
-        lo[j] = x - hi[j];
+        hi[j] = tf32_rn(x);
+        lo[j] = tf32_rn(x - hi[j]);
       }
       const uint32_t acol = tmem + lane_base + kTcColA + 64u * stg + 8u * ch;
       tmem_st8(acol, hi);
@@ -308,10 +318,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) moments3_tc_kernel(Moments3TcAr
         const int d = 4 * kc + e;
         y[e] = (c < k && d < nv) ? Ps[d * kp + c] : 0.f;
       }
-      const float4 hi = make_float4(tf32_hi(y[0]), tf32_hi(y[1]), tf32_hi(y[2]), tf32_hi(y[3]));
+      const float4 hi = make_float4(tf32_rn(y[0]), tf32_rn(y[1]), tf32_rn(y[2]), tf32_rn(y[3]));
       reinterpret_cast<float4*>(bbase)[slot] = hi;
       reinterpret_cast<float4*>(bbase + N * kTcDocs * 4)[slot] =
-          make_float4(y[0] - hi.x, y[1] - hi.y, y[2] - hi.z, y[3] - hi.w);
+          make_float4(tf32_rn(y[0] - hi.x), tf32_rn(y[1] - hi.y), tf32_rn(y[2] - hi.z),
+                      tf32_rn(y[3] - hi.w));
     }
     // the next step's weights (their buffer was last read in step i - 1); the lengths of
     // step i + 2 start loading
@@ -329,9 +340,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) moments3_tc_kernel(Moments3TcAr
       if (i + 2 < nsteps) fetch_rows(i + 2);
     }
     issued = i + 1;
-    // while these MMAs run: fold the previous pair's accumulator (steps i - 2, i - 1) into the
-    // running sum, which releases it for the pair starting at step i + 2
-    if (i >= 2 && (i & 1) == 0 && !merge(i - 1)) atomicExch(&s_abort, 1);
+    // while these MMAs run: fold the previous run's accumulator (ending at step i - 1) into the
+    // running sum, which releases it for the run starting at step i + kTcRun
+    if (i >= kTcRun && (i % kTcRun) == 0 && !merge(i - 1)) atomicExch(&s_abort, 1);
     asm volatile("tcgen05.fence::before_thread_sync;");
   }
   __syncthreads();

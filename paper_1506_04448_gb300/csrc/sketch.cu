@@ -766,6 +766,178 @@ static int launch_asym(const AsymSketchArgs& a0, int B, tsk_ctx* ctx) {
   return TSK_OK;
 }
 
+// ------------------------------------------------------------------ asymmetric build, exact int32
+// Complex-float asymmetric sketches (Eq. 1) by the colliding build's integer scheme: every entry
+// is rounded once to the grid 2^(E-25), 2^E > max|T| over the whole tensor (dense_absmax_kernel),
+// the real buckets are summed exactly in int32 shared memory with exact carries past 2^31, and
+// the slab partials are added in int64 by a fixed-order reduce, so that the result does not
+// depend on thread scheduling and the only other rounding is the final conversion to float.
+
+// max |T| over n entries, as the bit pattern of a non-negative float (monotone as unsigned);
+// NaN compares above every finite value, so a non-finite entry makes the result non-finite.
+template <typename TIn>
+__global__ void __launch_bounds__(256) dense_absmax_kernel(const TIn* T, long long count,
+                                                           unsigned* maxbits) {
+  unsigned m = 0u;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x)
+    m = max(m, __float_as_uint(fabsf((float)__ldcg(T + e))));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m != 0u) atomicMax(maxbits, m);
+}
+
+struct AsymFixArgs {
+  const void* T;
+  int n1, n2, n3, nmax;
+  const int32_t* h;   // [B][3][nmax]
+  const uint8_t* g;
+  int B;
+  int log2b;
+  long long rows;     // n1 * n2
+  int nslab;
+  const unsigned* maxbits;
+  int* carry;         // [B][b]: wraps of the int32 sums past +-2^31
+  int* part;          // [nslab][B][b]
+};
+
+// Per-mode word of index i: bucket h & (b - 1) in the low bits, the sign bit g & 1 in bit 31;
+// the sum of three words holds (h1 + h2 + h3) in its low 17 bits (b <= 2^15) and the parity of
+// g1 + g2 + g3, i.e. the sign of xi1 xi2 xi3, in bit 31.
+__device__ __forceinline__ uint32_t asym_word(int32_t h, uint8_t g, int mask) {
+  return (uint32_t)(h & mask) | ((uint32_t)(g & 1) << 31);
+}
+
+template <typename TIn>
+__global__ void __launch_bounds__(1024, 1) sketch_asym_fix_kernel(AsymFixArgs a) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const FixScale fs = fix_scale(*a.maxbits);
+  if (!fs.finite) return;   // the reduce kernel writes NaN
+  const int b = 1 << a.log2b;
+  const int mask = b - 1;
+  int* hist = reinterpret_cast<int*>(sm_raw);                                // [b]
+  uint32_t* ws = reinterpret_cast<uint32_t*>(sm_raw + (size_t)b * sizeof(int));  // [3][nmax]
+  const int m = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < b; i += nt) hist[i] = 0;
+  for (int i = tid; i < 3 * a.nmax; i += nt)
+    ws[i] = asym_word(a.h[(size_t)m * 3 * a.nmax + i], a.g[(size_t)m * 3 * a.nmax + i], mask);
+  __syncthreads();
+  const TIn* T = static_cast<const TIn*>(a.T);
+  const long long per_slab = (a.rows + a.nslab - 1) / a.nslab;
+  const long long r0 = (long long)blockIdx.y * per_slab;
+  const long long r1 = min(a.rows, r0 + per_slab);
+  const int nw = nt >> 5, w = tid >> 5, lane = tid & 31;
+  const uint32_t* w1 = ws;
+  const uint32_t* w2 = ws + a.nmax;
+  const uint32_t* w3 = ws + 2 * a.nmax;
+  const float sa = fs.sa, sb = fs.sb;
+  int* carry = a.carry + (size_t)m * b;
+  for (long long r = r0 + w; r < r1; r += nw) {
+    const int i = (int)(r / a.n2), j = (int)(r % a.n2);
+    const TIn* row = T + (size_t)r * a.n3;
+    const uint32_t wij = w1[i] + w2[j];
+    constexpr int kU = 4;
+    for (int k0 = lane; k0 < a.n3; k0 += 32 * kU) {
+      TIn x[kU];
+#pragma unroll
+      for (int q = 0; q < kU; ++q) {
+        const int k = k0 + 32 * q;
+        x[q] = k < a.n3 ? __ldcg(row + k) : (TIn)0;
+      }
+#pragma unroll
+      for (int q = 0; q < kU; ++q) {
+        const int k = k0 + 32 * q;
+        if (k >= a.n3) break;
+        const uint32_t sq = wij + w3[k];
+        float y = (float)x[q] * sa;
+        if (sb != 1.f) y *= sb;
+        const int v = __float2int_rn(__uint_as_float(__float_as_uint(y) ^ (sq & 0x80000000u)));
+        const int t = (int)(sq & (uint32_t)mask);
+        const int old = atomicAdd(&hist[t], v);
+        // |v| < 2^25 < 2^30: an add can wrap only if |old| >= 2^30; then the exact test, and a
+        // carry of +-2^32 to the global array (rare)
+        if ((int)((unsigned)old + 0x40000000u) < 0) {
+          const int sum = (int)((unsigned)old + (unsigned)v);
+          if (((old ^ sum) & (v ^ sum)) < 0) atomicAdd(&carry[t], v > 0 ? 1 : -1);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  int* dst = a.part + ((size_t)blockIdx.y * a.B + m) * b;
+  for (int c = tid; c < b; c += nt) dst[c] = hist[c];
+}
+
+// S[m][t] (+)= 2^(E-25) (sum over slabs of part[.][m][t] + 2^32 carry[m][t]) as the real part;
+// the imaginary part is 0 (or left as it is when accumulating).  NaN if max|T| is not finite
+// (also reported as TSK_ENONFINITE).
+__global__ void __launch_bounds__(256) asym_fix_reduce_kernel(const int* __restrict__ part,
+                                                              const int* __restrict__ carry,
+                                                              const unsigned* maxbits, int nslab,
+                                                              long long cells, float2* S,
+                                                              int accumulate, int* status) {
+  const FixScale fs = fix_scale(*maxbits);
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < cells;
+       c += (long long)gridDim.x * blockDim.x) {
+    float v;
+    if (fs.finite) {
+      long long acc = (long long)carry[c] * 4294967296LL;
+#pragma unroll 8
+      for (int s = 0; s < nslab; ++s) acc += __ldcg(part + (size_t)s * cells + c);
+      v = ldexpf(__ll2float_rn(acc), fs.e - kFixBits);
+    } else {
+      v = __int_as_float(0x7fc00000);
+      if (c == 0) tsk_set_status(status, TSK_ENONFINITE);
+    }
+    if (accumulate) {
+      S[c].x += v;
+    } else {
+      S[c] = make_float2(v, 0.f);
+    }
+  }
+}
+
+template <typename TIn>
+static int launch_asym_fix(const AsymSketchArgs& a0, int B, float2* S, int accumulate,
+                           tsk_ctx* ctx) {
+  const int b = 1 << a0.log2b;
+  const size_t smem = (size_t)b * sizeof(int) + (size_t)3 * a0.nmax * sizeof(uint32_t);
+  if (smem > (size_t)ctx->max_smem_optin) return TSK_EUNSUPPORTED;
+  auto kernel = sketch_asym_fix_kernel<TIn>;
+  TSK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  TSK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 1024, smem));
+  if (per_sm < 1) per_sm = 1;
+  long long nslab = ((long long)ctx->num_sms * per_sm) / B;
+  if (nslab < 1) nslab = 1;
+  const long long cap = (a0.rows * a0.n3 + 16383) / 16384;
+  if (nslab > cap) nslab = cap < 1 ? 1 : cap;
+  if (nslab > 65535) nslab = 65535;
+  AsymFixArgs a{a0.T, a0.n1, a0.n2, a0.n3, a0.nmax, a0.h, a0.g, B, a0.log2b, a0.rows,
+                (int)nslab, nullptr, nullptr, nullptr};
+  const size_t cells = (size_t)B * b;
+  const size_t head = ws_round(256) + ws_round(cells * sizeof(int));
+  int rc = tsk_ws_reserve(ctx, head + ws_round((size_t)a.nslab * cells * sizeof(int)));
+  if (rc != TSK_OK) return rc;
+  WsCarve wc{static_cast<char*>(ctx->ws), 0};
+  unsigned* maxbits = wc.take<unsigned>(64);
+  a.carry = wc.take<int>(cells);
+  a.part = wc.take<int>((size_t)a.nslab * cells);
+  a.maxbits = maxbits;
+  TSK_CUDA(cudaMemsetAsync(ctx->ws, 0, head, ctx->stream));
+  dense_absmax_kernel<TIn><<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(
+      static_cast<const TIn*>(a0.T), a0.rows * a0.n3, maxbits);
+  TSK_CHECK_LAUNCH();
+  kernel<<<dim3(B, (unsigned)a.nslab), 1024, smem, ctx->stream>>>(a);
+  TSK_CHECK_LAUNCH();
+  long long blocks = ((long long)cells + 255) / 256;
+  if (blocks > (long long)ctx->num_sms * 8) blocks = (long long)ctx->num_sms * 8;
+  asym_fix_reduce_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(
+      a.part, a.carry, maxbits, a.nslab, (long long)cells, S, accumulate, ctx->status);
+  TSK_CHECK_LAUNCH();
+  return TSK_OK;
+}
+
 // ------------------------------------------------------------------ batched DFT of sketches
 template <int LOGB>
 __global__ void __launch_bounds__(threads_for_logb(LOGB)) fft_rows_kernel(const float2* in,
@@ -968,17 +1140,19 @@ extern "C" int sketch_tensor(tsk_ctx* ctx, const void* T, int in_dtype, int M,
     const int n = (int)dims_host[0];
     return sketch_sym_planes(ctx, T, in_dtype, n, 0, n, h, g, B, log2b, S, acc_dtype, accumulate);
   }
-  if (!accumulate) TSK_CUDA(cudaMemsetAsync(S, 0, (size_t)B * b * 2 * elem, ctx->stream));
   const int n1 = (int)dims_host[0], n2 = (int)dims_host[1], n3 = (int)dims_host[2];
-  if (n1 == 0 || n2 == 0 || n3 == 0) return TSK_OK;
   const int nmax = n1 > n2 ? (n1 > n3 ? n1 : n3) : (n2 > n3 ? n2 : n3);
   AsymSketchArgs a{T, n1, n2, n3, nmax, h, g, log2b, (long long)n1 * n2, 1, S};
-  if (acc_dtype == TSK_C64) {
+  if (acc_dtype == TSK_C64 && n1 > 0 && n2 > 0 && n3 > 0) {
+    // complex-float sketches: exact int32 accumulation (writes or adds S itself)
     if (log2b > 15) return TSK_EUNSUPPORTED;
-    if (in_dtype == TSK_F32) return launch_asym<float, float>(a, B, ctx);
-    if (in_dtype == TSK_F64) return launch_asym<double, float>(a, B, ctx);
-    return launch_asym<int32_t, float>(a, B, ctx);
+    float2* Sf = static_cast<float2*>(S);
+    if (in_dtype == TSK_F32) return launch_asym_fix<float>(a, B, Sf, accumulate, ctx);
+    if (in_dtype == TSK_F64) return launch_asym_fix<double>(a, B, Sf, accumulate, ctx);
+    return launch_asym_fix<int32_t>(a, B, Sf, accumulate, ctx);
   }
+  if (!accumulate) TSK_CUDA(cudaMemsetAsync(S, 0, (size_t)B * b * 2 * elem, ctx->stream));
+  if (n1 == 0 || n2 == 0 || n3 == 0) return TSK_OK;
   if (log2b > 14) return TSK_EUNSUPPORTED;
   if (acc_dtype == TSK_C128) {
     if (in_dtype == TSK_F32) return launch_asym<float, double>(a, B, ctx);

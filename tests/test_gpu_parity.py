@@ -167,6 +167,66 @@ def test_asymmetric_sketch(dev, dims, log2b):
             assert not Si[m, :, 1].any()
 
 
+@pytest.mark.parametrize("scale", [1e-30, 1.0, 1e30])
+def test_asymmetric_float_sketch_exact_integer_build(dev, scale):
+    """Complex-float asymmetric sketches are summed in exact integers on the grid set by max|T|:
+    two builds are bit-identical, tiny and huge tensors keep the relative accuracy, accumulate
+    adds the real parts and keeps the imaginary parts, and FP64 and int32 inputs take the same
+    path."""
+    dims, log2b, B = (31, 26, 45), 11, 3
+    b = 1 << log2b
+    r = synth.rng(77)
+    T = r.standard_normal(dims) * scale
+    h, g = tsk.cs_hashes(5, B, log2b, list(dims), dev)
+    ho, go = O.cs_hashes(5, B, log2b, list(dims))
+    Td = t32(T, dev)
+    S = tsk.sketch_tensor(Td, h, g, log2b)
+    S2 = tsk.sketch_tensor(Td, h, g, log2b)
+    assert torch.equal(S, S2)
+    Sn = S.cpu().numpy()
+    assert not Sn.imag.any()
+    T32 = T.astype(np.float32).astype(np.float64)
+    for m in range(B):
+        assert rel(Sn[m], O.sketch_tensor_asym(T32, ho[m], go[m], b)) < 1e-5
+    acc = torch.full_like(S, complex(1.0, 2.0))
+    tsk.sketch_tensor(Td, h, g, log2b, S=acc, accumulate=True)
+    an = acc.cpu().numpy()
+    np.testing.assert_array_equal(an.imag, 2.0)
+    np.testing.assert_allclose(an.real, Sn.real + 1.0, rtol=0, atol=1e-6 * (1 + np.abs(Sn.real).max()))
+    S64 = tsk.sketch_tensor(torch.tensor(T, device=dev), h, g, log2b).cpu().numpy()
+    for m in range(B):
+        assert rel(S64[m], O.sketch_tensor_asym(T, ho[m], go[m], b)) < 1e-5
+    if scale == 1.0:
+        Ti = r.integers(-1000, 1000, size=dims).astype(np.int32)
+        Si = tsk.sketch_tensor(torch.tensor(Ti, device=dev), h, g, log2b).cpu().numpy()
+        for m in range(B):
+            assert rel(Si[m], O.sketch_tensor_asym(Ti.astype(np.float64), ho[m], go[m], b)) < 1e-6
+
+
+def test_asymmetric_sketch_with_carries_and_nonfinite(dev):
+    """Entries of near-maximal magnitude whose signs cancel sketch 0's signs xi1 xi2 xi3, into
+    few buckets (b = 2^6): every add to a bucket of sketch 0 has the same sign, the int32 bucket
+    sums pass 2^31 many times, and the exact carries keep the result; then a NaN entry makes the
+    sketch NaN and is reported as TSK_ENONFINITE."""
+    dims, log2b, B = (64, 64, 64), 6, 2
+    b = 1 << log2b
+    h, g = tsk.cs_hashes(3, B, log2b, list(dims), dev)
+    ho, go = O.cs_hashes(3, B, log2b, list(dims))
+    xi = [1.0 - 2.0 * (go[0, j, :dims[j]] & 1) for j in range(3)]
+    T = 0.999 * np.einsum("i,j,k->ijk", xi[0], xi[1], xi[2])
+    Td = t32(T, dev)
+    S = tsk.sketch_tensor(Td, h, g, log2b).cpu().numpy()
+    T32 = T.astype(np.float32).astype(np.float64)
+    for m in range(B):
+        assert rel(S[m], O.sketch_tensor_asym(T32, ho[m], go[m], b)) < 1e-6
+    tsk.check_status(dev)
+    Td[1, 2, 3] = float("nan")
+    S = tsk.sketch_tensor(Td, h, g, log2b).cpu().numpy()
+    assert np.isnan(S.real).all()
+    assert tsk.ctx_status(dev) == -5     # TSK_ENONFINITE
+    tsk.check_status(dev)
+
+
 # ------------------------------------------------------------------ DFT
 @pytest.mark.parametrize("log2b", [8, 9, 10, 11, 12, 13, 14])
 def test_sketch_fft(dev, log2b):
