@@ -76,15 +76,16 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mbar) : "memory");
 }
 
-// x rounded to TF32 (10 explicit mantissa bits), to nearest.  The split x = hi + lo uses
+// x rounded to TF32 (10 explicit mantissa bits), to nearest with ties away from zero: adding
+// half a unit of the 13 dropped bits to the magnitude bits and clearing them carries into the
+// exponent when it should (finite x well below the float range).  The split x = hi + lo uses
 // hi = tf32_rn(x) and lo = tf32_rn(x - hi): x - hi is exact in FP32 and at most 2^-11 |x|, and
 // rounding it costs at most 2^-22 |x|.  Both roundings are to nearest, so that their errors do
 // not add up with one sign over the many documents of a sum (truncation would: a bias of about
-// 2^-21 per product, which the cancellation between the moment's terms magnifies).
+// 2^-21 per product, which the cancellation between the moment's terms magnifies).  Two integer
+// operations, on the full-rate ALU.
 __device__ __forceinline__ float tf32_rn(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
 }
 
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {

@@ -832,36 +832,77 @@ __global__ void __launch_bounds__(1024, 1) sketch_asym_fix_kernel(AsymFixArgs a)
   const uint32_t* w3 = ws + 2 * a.nmax;
   const float sa = fs.sa, sb = fs.sb;
   int* carry = a.carry + (size_t)m * b;
-  for (long long r = r0 + w; r < r1; r += nw) {
-    const int i = (int)(r / a.n2), j = (int)(r % a.n2);
-    const TIn* row = T + (size_t)r * a.n3;
-    const uint32_t wij = w1[i] + w2[j];
-    constexpr int kU = 4;
-    for (int k0 = lane; k0 < a.n3; k0 += 32 * kU) {
-      TIn x[kU];
+  // The warp's work is a list of chunks (row r, kU 32-entry pieces of it), walked with
+  // incremental cursors (no divisions in the loop); the loads of the next chunk are issued before
+  // the adds of the current one, so that every lane keeps 2 kU loads in flight while it waits on
+  // shared adds.  Rows number at most 8192^2, so int indices suffice.
+  constexpr int kU = 4;
+  const int cpr = (a.n3 + 32 * kU - 1) / (32 * kU);          // chunks per row
+  const int rend = (int)r1;
+  int r = (int)r0 + w, kc = 0;                                // chunk being processed
+  int i = r / a.n2, jj = r % a.n2;                            // its row's (i, j)
+  int rn = r, kcn = 0;                                        // chunk being loaded
+  auto load_chunk = [&](int rr, int kk, TIn* x) {
+    const TIn* row = T + (size_t)rr * a.n3;
+    const int k0 = kk * 32 * kU + lane;
+#pragma unroll
+    for (int q = 0; q < kU; ++q) {
+      const int k = k0 + 32 * q;
+      x[q] = k < a.n3 ? __ldcg(row + k) : (TIn)0;
+    }
+  };
+  auto step = [&](int& rr, int& kk) {
+    if (++kk == cpr) { kk = 0; rr += nw; }
+  };
+  TIn xc[kU];
+  if (rn < rend) {
+    load_chunk(rn, kcn, xc);
+    step(rn, kcn);
+  }
+  while (r < rend) {
+    TIn xn[kU];
+    if (rn < rend) load_chunk(rn, kcn, xn);
+    const uint32_t wij = w1[i] + w2[jj];
+    const int k0 = kc * 32 * kU + lane;
+    int v[kU], t[kU], old[kU];
+#pragma unroll
+    for (int q = 0; q < kU; ++q) {
+      const int k = k0 + 32 * q;
+      const uint32_t sq = wij + w3[k < a.n3 ? k : 0];
+      float y = (float)xc[q] * sa;
+      if (sb != 1.f) y *= sb;
+      v[q] = __float2int_rn(__uint_as_float(__float_as_uint(y) ^ (sq & 0x80000000u)));
+      t[q] = (int)(sq & (uint32_t)mask);
+    }
+    // the chunk's adds back to back (lanes beyond the row issue none); the returned values are
+    // examined after the last one
+#pragma unroll
+    for (int q = 0; q < kU; ++q) {
+      old[q] = 0;
+      if (k0 + 32 * q < a.n3) old[q] = atomicAdd(&hist[t[q]], v[q]);
+    }
+    // |v| < 2^25 < 2^30: an add can wrap only if |old| >= 2^30; then the exact test, and a
+    // carry of +-2^32 to the global array (rare)
+    unsigned near = 0u;
+#pragma unroll
+    for (int q = 0; q < kU; ++q) near |= (unsigned)old[q] + 0x40000000u;
+    if ((int)near < 0) {
 #pragma unroll
       for (int q = 0; q < kU; ++q) {
-        const int k = k0 + 32 * q;
-        x[q] = k < a.n3 ? __ldcg(row + k) : (TIn)0;
-      }
-#pragma unroll
-      for (int q = 0; q < kU; ++q) {
-        const int k = k0 + 32 * q;
-        if (k >= a.n3) break;
-        const uint32_t sq = wij + w3[k];
-        float y = (float)x[q] * sa;
-        if (sb != 1.f) y *= sb;
-        const int v = __float2int_rn(__uint_as_float(__float_as_uint(y) ^ (sq & 0x80000000u)));
-        const int t = (int)(sq & (uint32_t)mask);
-        const int old = atomicAdd(&hist[t], v);
-        // |v| < 2^25 < 2^30: an add can wrap only if |old| >= 2^30; then the exact test, and a
-        // carry of +-2^32 to the global array (rare)
-        if ((int)((unsigned)old + 0x40000000u) < 0) {
-          const int sum = (int)((unsigned)old + (unsigned)v);
-          if (((old ^ sum) & (v ^ sum)) < 0) atomicAdd(&carry[t], v > 0 ? 1 : -1);
-        }
+        const int sum = (int)((unsigned)old[q] + (unsigned)v[q]);
+        if (((old[q] ^ sum) & (v[q] ^ sum)) < 0) atomicAdd(&carry[t[q]], v[q] > 0 ? 1 : -1);
       }
     }
+#pragma unroll
+    for (int q = 0; q < kU; ++q) xc[q] = xn[q];
+    // next chunk: the row's (i, j) move on by nw rows when the row changes
+    if (++kc == cpr) {
+      kc = 0;
+      r += nw;
+      jj += nw;
+      while (jj >= a.n2) { jj -= a.n2; ++i; }
+    }
+    if (rn < rend) step(rn, kcn);
   }
   __syncthreads();
   int* dst = a.part + ((size_t)blockIdx.y * a.B + m) * b;
