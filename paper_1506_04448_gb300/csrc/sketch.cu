@@ -407,32 +407,36 @@ __device__ __forceinline__ void sym_fix_rows_edge(const SymFixArgs& a, const Fix
 }
 
 // The tiles of one block: planes [i0, i1), row blocks rb >= rb0 = i0 / 32, columns c >= rb,
-// planes i < 32 rb + 32 only.  For row block rb there are (min(i1, 32 rb + 32) - i0) planes
-// times (nc - rb) columns; pre[] holds the running counts.
+// planes i < 32 rb + 32 only.  For row block rb there are nir = min(i1, 32 rb + 32) - i0 planes
+// times (nc - rb) columns; pre[] holds the running counts and rcp[] the reciprocals 1 / nir.
+// A warp's items come from the block's counter in increasing order, so its row block only moves
+// forward (a scan from the last one), and local / nir is a float product corrected to the exact
+// quotient (local < 2^24).
 template <typename TIn, int SK, bool RANGES, bool TWO>
 __device__ __forceinline__ void sym_fix_tiles(const SymFixArgs& a, const FixScale& fs, int* hist,
-                                              const uint32_t* qs, const int* pre, int nrb,
-                                              int* next, int i0, int i1, int m0, int rr) {
+                                              const uint32_t* qs, const int* pre,
+                                              const float* rcp, int nrb, int* next, int i0,
+                                              int i1, int m0, int rr) {
   const int n = a.n;
   const int rb0 = i0 >> 5;
   const int lane = threadIdx.x & 31;
   const TIn* T = static_cast<const TIn*>(a.T);
   const int items = pre[nrb];
+  int lo = 0;   // row block of the warp's last item
   for (;;) {
     int it = 0;
     if (lane == 0) it = atomicAdd(next, 1);
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= items) break;
-    int lo = 0, hi = nrb - 1;   // row block: last with pre[.] <= it
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (pre[mid] <= it) lo = mid; else hi = mid - 1;
-    }
+    while (pre[lo + 1] <= it) ++lo;   // row block: last with pre[.] <= it
     const int rb = rb0 + lo;
     const int nir = min(i1, 32 * rb + 32) - i0;
     const int local = it - pre[lo];
-    const int c = rb + local / nir;
-    const int i = i0 + local % nir;
+    int cq = (int)((float)local * rcp[lo]);
+    int ir = local - cq * nir;
+    if (ir < 0) { --cq; ir += nir; } else if (ir >= nir) { ++cq; ir -= nir; }
+    const int c = rb + cq;
+    const int i = i0 + ir;
     const int jlo = max(i, 32 * rb), jhi = min(32 * rb + 32, n);
     const int k = 32 * c + lane;
     // last row this lane takes part in: the tile's last row, k itself on the diagonal block
@@ -442,7 +446,9 @@ __device__ __forceinline__ void sym_fix_tiles(const SymFixArgs& a, const FixScal
     // spread like everyone else's (one shared cell would serialise those adds)
     uint32_t qik[SK];
 #pragma unroll
-    for (int s = 0; s < SK; ++s) qik[s] = qs[s * n + i] + qs[s * n + (k < n ? k : k % n)];
+    int kw = k;   // k mod n (k < n + 32)
+    while (kw >= n) kw -= n;
+    for (int s = 0; s < SK; ++s) qik[s] = qs[s * n + i] + qs[s * n + kw];
     const TIn* col = T + ((size_t)i * n + jlo) * n + (k < n ? k : n - 1);
     if (jlo > i && rb < c && ((jhi - jlo) & 7) == 0)
       sym_fix_rows_interior<TIn, SK, RANGES, TWO>(a, fs, hist, qs, col, k < n, jlo, jhi, qik, m0, rr);
@@ -460,6 +466,7 @@ __global__ void __launch_bounds__(1024, 1) sketch_sym_fix_kernel(SymFixArgs a) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ int s_next;
   __shared__ int s_pre[kMaxTileCols + 1];
+  __shared__ float s_rcp[kMaxTileCols];
   const FixScale fs = fix_scale(*a.maxbits);
   if (!fs.finite) return;   // the reduce kernel writes NaN
   const int b = 1 << a.log2b;
@@ -489,15 +496,19 @@ __global__ void __launch_bounds__(1024, 1) sketch_sym_fix_kernel(SymFixArgs a) {
     for (int q = 0; q < nrb; ++q) {
       s_pre[q] = acc;
       const int rb = rb0 + q;
-      acc += (min(i1, 32 * rb + 32) - i0) * (nc - rb);
+      const int nir = min(i1, 32 * rb + 32) - i0;
+      s_rcp[q] = 1.f / (float)nir;
+      acc += nir * (nc - rb);
     }
     s_pre[nrb] = acc;
   }
   __syncthreads();
   if (fs.sb == 1.f)
-    sym_fix_tiles<TIn, SK, RANGES, false>(a, fs, hist, qs, s_pre, nrb, &s_next, i0, i1, m0, rr);
+    sym_fix_tiles<TIn, SK, RANGES, false>(a, fs, hist, qs, s_pre, s_rcp, nrb, &s_next, i0, i1, m0,
+                                          rr);
   else
-    sym_fix_tiles<TIn, SK, RANGES, true>(a, fs, hist, qs, s_pre, nrb, &s_next, i0, i1, m0, rr);
+    sym_fix_tiles<TIn, SK, RANGES, true>(a, fs, hist, qs, s_pre, s_rcp, nrb, &s_next, i0, i1, m0,
+                                         rr);
   __syncthreads();
   for (int s = 0; s < SK; ++s) {
     int* dst = a.part + ((size_t)blockIdx.y * a.B + (m0 + s)) * 2 * b + (size_t)2 * rr * br;
@@ -506,27 +517,51 @@ __global__ void __launch_bounds__(1024, 1) sketch_sym_fix_kernel(SymFixArgs a) {
 }
 
 // S[m][c] (+)= 2^(E-25) (sum over slabs of part[.][m][c] + 2^32 carry[m][c]); NaN if max|T| is
-// not finite (also reported as TSK_ENONFINITE).
+// not finite (also reported as TSK_ENONFINITE).  Four cells per thread with 16-byte loads
+// (cells is a multiple of 4), so that one wave of threads has every slab's loads in flight.
 __global__ void __launch_bounds__(256) sym_fix_reduce_kernel(const int* __restrict__ part,
                                                              const int* __restrict__ carry,
                                                              const unsigned* maxbits, int nslab,
                                                              long long cells, float* S,
-                                                             int accumulate, int* status) {
+                                                             int accumulate, int s_aligned,
+                                                             int* status) {
   const FixScale fs = fix_scale(*maxbits);
-  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < cells;
-       c += (long long)gridDim.x * blockDim.x) {
-    float v;
+  const long long quads = cells >> 2;
+  for (long long c4 = (long long)blockIdx.x * blockDim.x + threadIdx.x; c4 < quads;
+       c4 += (long long)gridDim.x * blockDim.x) {
+    float v[4];
     if (fs.finite) {
-      long long acc = (long long)carry[c] * 4294967296LL;
+      const int4 cr = __ldcg(reinterpret_cast<const int4*>(carry) + c4);
+      long long acc[4] = {(long long)cr.x * 4294967296LL, (long long)cr.y * 4294967296LL,
+                          (long long)cr.z * 4294967296LL, (long long)cr.w * 4294967296LL};
 #pragma unroll 8
-      for (int s = 0; s < nslab; ++s) acc += __ldcg(part + (size_t)s * cells + c);
+      for (int s = 0; s < nslab; ++s) {
+        const int4 p = __ldcg(reinterpret_cast<const int4*>(part + (size_t)s * cells) + c4);
+        acc[0] += p.x;
+        acc[1] += p.y;
+        acc[2] += p.z;
+        acc[3] += p.w;
+      }
       // one rounding (int64 -> float), then an exact power-of-two scaling
-      v = ldexpf(__ll2float_rn(acc), fs.e - kFixBits);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[e] = ldexpf(__ll2float_rn(acc[e]), fs.e - kFixBits);
     } else {
-      v = __int_as_float(0x7fc00000);
-      if (c == 0) tsk_set_status(status, TSK_ENONFINITE);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[e] = __int_as_float(0x7fc00000);
+      if (c4 == 0) tsk_set_status(status, TSK_ENONFINITE);
     }
-    S[c] = accumulate ? S[c] + v : v;
+    if (s_aligned) {
+      float4* S4 = reinterpret_cast<float4*>(S) + c4;
+      if (accumulate) {
+        const float4 o = *S4;
+        *S4 = make_float4(o.x + v[0], o.y + v[1], o.z + v[2], o.w + v[3]);
+      } else {
+        *S4 = make_float4(v[0], v[1], v[2], v[3]);
+      }
+    } else {   // S is only 8-byte aligned (a complex-float array)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) S[4 * c4 + e] = accumulate ? S[4 * c4 + e] + v[e] : v[e];
+    }
   }
 }
 
@@ -733,11 +768,11 @@ static int launch_sym_fix(const void* T, int n, int p0, int p1, const int32_t* h
     else rc = launch_sym_fix_t<TIn, 1, true>(a, groups, smem, ctx);
   }
   if (rc != TSK_OK) return rc;
-  long long blocks = ((long long)cells + 255) / 256;
+  long long blocks = ((long long)cells / 4 + 255) / 256;
   if (blocks > (long long)ctx->num_sms * 8) blocks = (long long)ctx->num_sms * 8;
   sym_fix_reduce_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(
       a.part, a.carry, maxbits, a.nslab, (long long)cells, static_cast<float*>(S), accumulate,
-      ctx->status);
+      (reinterpret_cast<uintptr_t>(S) & 15) == 0 ? 1 : 0, ctx->status);
   TSK_CHECK_LAUNCH();
   return TSK_OK;
 }

@@ -119,6 +119,24 @@ def test_symmetric_sketch_any_magnitude(dev, scale):
         assert rel(S[m], O.sketch_tensor_sym(T32, ho[m, 0], go[m, 0], b)) < 1e-5
 
 
+def test_symmetric_sketch_into_unaligned_output(dev):
+    """S only 8-byte aligned (a complex-float array starting at an odd element): the reduce's
+    16-byte stores fall back to scalar stores; write and accumulate both match the aligned
+    result bit for bit."""
+    n, log2b, B = 40, 10, 3
+    b = 1 << log2b
+    T = t32(synth.random_symmetric(n, 12), dev)
+    h, g = tsk.cs_hashes(21, B, log2b, [n], dev)
+    ref = tsk.sketch_tensor(T, h, g, log2b)
+    buf = torch.zeros(B * b + 1, dtype=torch.complex64, device=dev)
+    S = buf[1:].view(B, b)
+    assert S.data_ptr() % 16 == 8
+    tsk.sketch_tensor(T, h, g, log2b, S=S)
+    assert torch.equal(S, ref)
+    tsk.sketch_tensor(T, h, g, log2b, S=S, accumulate=True)
+    assert torch.equal(S, ref + ref)
+
+
 def test_symmetric_sketch_of_zero_and_nonfinite_tensors(dev):
     n, log2b, B = 9, 8, 2
     h, g = tsk.cs_hashes(4, B, log2b, [n], dev)
