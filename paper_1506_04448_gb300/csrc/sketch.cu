@@ -444,16 +444,35 @@ __device__ __forceinline__ void sym_fix_tiles(const SymFixArgs& a, const FixScal
     const int jlim = k >= n ? -1 : (rb == c ? min(k, jhi - 1) : jhi - 1);
     // a lane beyond the tensor adds zeros; it takes the word of k mod n, so that its cells are
     // spread like everyone else's (one shared cell would serialise those adds)
-    uint32_t qik[SK];
-#pragma unroll
     int kw = k;   // k mod n (k < n + 32)
     while (kw >= n) kw -= n;
+    uint32_t qik[SK];
+#pragma unroll
     for (int s = 0; s < SK; ++s) qik[s] = qs[s * n + i] + qs[s * n + kw];
     const TIn* col = T + ((size_t)i * n + jlo) * n + (k < n ? k : n - 1);
-    if (jlo > i && rb < c && ((jhi - jlo) & 7) == 0)
-      sym_fix_rows_interior<TIn, SK, RANGES, TWO>(a, fs, hist, qs, col, k < n, jlo, jhi, qik, m0, rr);
-    else
+    if (rb < c) {
+      // off the diagonal block: the plane's first row (j = i, kappa 3) and enough rows after it
+      // to leave whole 8-row batches go the per-row path, the batches the interior path
+      // (kappa 6), a ragged tail the per-row path again
+      int e = 0;
+      if (jlo == i) {
+        e = (jhi - i) & 7;
+        if (e == 0) e = 8;
+      }
+      const int jmid = jlo + e;
+      const int nint = (jhi - jmid) & ~7;
+      if (e > 0)
+        sym_fix_rows_edge<TIn, SK, RANGES, TWO>(a, fs, hist, qs, col, i, k, jlo, jmid,
+                                                min(jlim, jmid - 1), qik, m0, rr);
+      if (nint > 0)
+        sym_fix_rows_interior<TIn, SK, RANGES, TWO>(a, fs, hist, qs, col + (size_t)e * n, k < n,
+                                                    jmid, jmid + nint, qik, m0, rr);
+      if (jmid + nint < jhi)
+        sym_fix_rows_edge<TIn, SK, RANGES, TWO>(a, fs, hist, qs, col + (size_t)(e + nint) * n, i,
+                                                k, jmid + nint, jhi, jlim, qik, m0, rr);
+    } else {
       sym_fix_rows_edge<TIn, SK, RANGES, TWO>(a, fs, hist, qs, col, i, k, jlo, jhi, jlim, qik, m0, rr);
+    }
   }
 }
 
