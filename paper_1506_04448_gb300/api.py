@@ -227,6 +227,66 @@ def allreduce_sketches(S: torch.Tensor, group=None) -> torch.Tensor:
     return S
 
 
+def select_first_max(lams, taus) -> int:
+    """Index q of the largest lams[q], ties to the smallest global initial-vector index taus[q]:
+    Alg. 1's selection (the first maximum over tau) taken over shards of the L initial vectors,
+    each of which reports its own first maximum (lam, tau).  Host-side only."""
+    best = 0
+    for q in range(1, len(lams)):
+        if lams[q] > lams[best] or (lams[q] == lams[best] and taus[q] < taus[best]):
+            best = q
+    return best
+
+
+def _library_round(S, h, g, U0_round, T):
+    res = robust_power_method(S, h, g, U0_round.unsqueeze(0), T, return_deflated=True)
+    return float(res["lam"][0].item()), int(res["tau"][0].item()), res["V"][0], res["S_deflated"]
+
+
+def robust_power_method_sharded(S: torch.Tensor, h: torch.Tensor, g: torch.Tensor,
+                                U0_local: torch.Tensor, T: int, tau_offset: int, group=None,
+                                run_round=None):
+    """Alg. 1 with the L initial vectors of every round split across the ranks of a
+    torch.distributed process group.  Every rank holds the same sketches S [B][b] and its slice
+    U0_local = U0[:, tau_offset:tau_offset + L_local] [k][L_local][n].  Per round each rank runs
+    T power updates of its vectors and selects its first maximum (run_round, by default one round
+    of robust_power_method on the device, which also deflates by its own choice in FP64); one
+    all-gather of (lambda, global tau) picks the round's winner (select_first_max), and the winner
+    broadcasts its component and its deflated sketches, which every rank continues from.  The
+    result equals Alg. 1 on all L vectors.  Returns dict(lam [k] float64, V [k][n], tau [k] int64
+    (global indices), S_deflated).
+
+    run_round(S, U0_round_local [L_local][n], T) -> (lam, tau_local, v [n], S_deflated) may
+    replace the device round (the host test of the exchange uses the oracle)."""
+    import torch.distributed as dist
+    if run_round is None:
+        def run_round(S_, U0_round, T_):
+            return _library_round(S_, h, g, U0_round, T_)
+    world = dist.get_world_size(group)
+    ranks = [dist.get_global_rank(group, q) if group is not None else q for q in range(world)]
+    k = U0_local.shape[0]
+    lam = torch.empty(k, dtype=torch.float64)
+    tau = torch.empty(k, dtype=torch.int64)
+    Vs = []
+    for r in range(k):
+        lam_r, tau_r, v, Sd = run_round(S, U0_local[r], T)
+        key = torch.tensor([lam_r, float(tau_offset + tau_r)], dtype=torch.float64, device=v.device)
+        keys = [torch.empty_like(key) for _ in range(world)]
+        dist.all_gather(keys, key, group=group)
+        keys = [kk.cpu() for kk in keys]
+        win = select_first_max([float(kk[0]) for kk in keys], [float(kk[1]) for kk in keys])
+        v = v.clone().contiguous()
+        Sd = Sd.clone().contiguous()
+        dist.broadcast(v, src=ranks[win], group=group)
+        dist.broadcast(torch.view_as_real(Sd) if Sd.is_complex() else Sd, src=ranks[win],
+                       group=group)
+        lam[r] = float(keys[win][0])
+        tau[r] = int(keys[win][1])
+        Vs.append(v)
+        S = Sd
+    return {"lam": lam, "V": torch.stack(Vs) if Vs else None, "tau": tau, "S_deflated": S}
+
+
 def sketch_fft(S: torch.Tensor, inverse: bool = False, out: torch.Tensor | None = None):
     """Batched DFT of the rows of a complex64 [B][b] tensor (inverse includes 1/b)."""
     device = S.device

@@ -1,7 +1,8 @@
 """Sketches sharded by planes (Sec. 3.1 linearity): the colliding sketch of the wedge entries
 whose first index lies in a plane range, built from that slice of the tensor alone, equals the
 oracle's sketch of the tensor masked to those entries, and the partial sketches of a partition
-of the planes add up to the sketch of the whole tensor.
+of the planes add up to the sketch of the whole tensor.  Alg. 1 with the initial vectors split
+into shards (robust_power_method_sharded) equals Alg. 1 on all of them.
 
 Tolerances: int64 sketches bit-exact, FP64 sketches 1e-12 relative, FP32 (complex64) sketches
 1e-5 relative in the 2-norm per sketch.
@@ -109,3 +110,69 @@ def test_empty_range_and_bad_ranges(dev):
     assert torch.equal(S1, S2)
     with pytest.raises(ValueError):
         tsk.sketch_tensor_planes(T[0:5].contiguous(), h, g, log2b, 8)
+
+
+# ------------------------------------------------------------------ Alg. 1 with the initial vectors split
+def _planted_problem(dev, n=50, k=4, B=5, log2b=10, L=8, seed=3):
+    T, _, _ = synth.planted_symmetric(n, k, 0.001, seed, dtype=np.float32)
+    h, g = tsk.cs_hashes(seed, B, log2b, [n], dev)
+    S = tsk.sketch_tensor(torch.from_numpy(T).to(dev), h, g, log2b)
+    U0 = torch.from_numpy(synth.gaussian_inits(k, L, n, seed + 1).astype(np.float32)).to(dev)
+    return S, h, g, U0
+
+
+def _check_round(ref, r, lam_r, tau_r, v_r):
+    lam_ref = float(ref["lam"][r])
+    row = ref["lam_all"][r].double().cpu()
+    assert abs(lam_r - lam_ref) <= 1e-5 * abs(lam_ref)
+    assert float(row[tau_r]) >= float(row.max()) - 1e-5 * abs(float(row.max()))
+    assert abs(float(torch.dot(v_r.double(), ref["V"][r].double()))) >= 1 - 1e-6
+
+
+def test_rounds_over_two_shards_equal_alg1(dev):
+    """Every round's L initial vectors split into two shards, each run by one round of the device
+    Alg. 1 (robust_power_method with k = 1), the winner chosen by select_first_max and its
+    deflated sketches carried on: the same eigenvalues, global taus and components as Alg. 1 on
+    all L vectors (the exchange robust_power_method_sharded makes over a process group).  Several
+    starts converge to the same component with eigenvalues equal to rounding, and the shared-memory
+    float adds of the count sketches make that rounding run-dependent, so the chosen tau is
+    checked to attain the round's maximum within 1e-5 rather than to equal the reference's."""
+    S, h, g, U0 = _planted_problem(dev)
+    T_it = 20
+    ref = tsk.robust_power_method(S, h, g, U0, T_it, return_deflated=True, return_trace=True)
+    k, L, n = U0.shape
+    shards = [(0, 3), (3, L)]                      # uneven on purpose
+    Sc = S.clone()
+    for r in range(k):
+        outs = []
+        for lo, hi in shards:
+            res = tsk.robust_power_method(Sc, h, g, U0[r:r + 1, lo:hi].contiguous(), T_it,
+                                          return_deflated=True)
+            outs.append((float(res["lam"][0]), lo + int(res["tau"][0]), res["V"][0],
+                         res["S_deflated"]))
+        win = tsk.select_first_max([o[0] for o in outs], [o[1] for o in outs])
+        lam_r, tau_r, v_r, Sc = outs[win]
+        _check_round(ref, r, lam_r, tau_r, v_r)
+    assert rel(Sc.cpu().numpy(), ref["S_deflated"].cpu().numpy()) < 1e-4
+
+
+def test_sharded_alg1_over_an_nccl_group_of_one(dev):
+    """robust_power_method_sharded through real NCCL collectives (a process group of one rank on
+    this GPU): equal to robust_power_method."""
+    import os
+    import socket
+    import torch.distributed as dist
+    os.environ.setdefault("NCCL_NVLS_ENABLE", "0")
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
+    try:
+        S, h, g, U0 = _planted_problem(dev, seed=5)
+        ref = tsk.robust_power_method(S, h, g, U0, 15, return_deflated=True, return_trace=True)
+        res = tsk.robust_power_method_sharded(S, h, g, U0, 15, 0)
+        for r in range(U0.shape[0]):
+            _check_round(ref, r, float(res["lam"][r]), int(res["tau"][r]), res["V"][r])
+        assert rel(res["S_deflated"].cpu().numpy(), ref["S_deflated"].cpu().numpy()) < 1e-4
+    finally:
+        dist.destroy_process_group()

@@ -97,3 +97,64 @@ def test_two_gloo_ranks_sum_partial_sketches():
         ok_i, err_f, _ = res[r]
         assert ok_i
         assert err_f < 1e-12
+
+
+# ------------------------------------------------------------------ Alg. 1 with the initial vectors split
+def test_select_first_max_ties_to_smallest_index():
+    from paper_1506_04448_gb300 import select_first_max
+    assert select_first_max([1.0, 3.0, 2.0], [0, 4, 8]) == 1
+    assert select_first_max([3.0, 3.0, 2.0], [4, 0, 8]) == 1
+    assert select_first_max([-1.0], [5]) == 0
+
+
+def _rtpm_rank(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import oracle as O
+    import synth
+    from paper_1506_04448_gb300 import robust_power_method_sharded
+    n, k, L, T_it, B, log2b = 12, 3, 6, 5, 3, 7
+    b = 1 << log2b
+    Tn, _, _ = synth.planted_symmetric(n, k, 0.05, 23)
+    ho, go = O.cs_hashes(9, B, log2b, [n])
+    h, g = ho[:, 0], go[:, 0]
+    S = np.stack([O.sketch_tensor_sym(Tn, h[m], g[m], b) for m in range(B)])
+    U0 = synth.gaussian_inits(k, L, n, 24)
+    per = L // world
+    lo = rank * per
+
+    def oracle_round(Sc, U0_round, T):
+        res = O.rtpm_sketched(Sc.numpy(), h, g, b, U0_round.numpy()[None], T)
+        return (float(res["lam"][0]), int(res["tau"][0]), torch.from_numpy(res["V"][0].copy()),
+                torch.from_numpy(res["S_deflated"].copy()))
+
+    res = robust_power_method_sharded(torch.from_numpy(S), None, None,
+                                      torch.from_numpy(U0[:, lo:lo + per].copy()), T_it, lo,
+                                      run_round=oracle_round)
+    ref = O.rtpm_sketched(S, h, g, b, U0, T_it)
+    out[rank] = (res["lam"].numpy().tolist(), res["tau"].numpy().tolist(),
+                 float(np.abs(res["V"].numpy() - ref["V"]).max()),
+                 float(np.abs(res["S_deflated"].numpy() - ref["S_deflated"]).max()),
+                 ref["lam"].tolist(), ref["tau"].tolist())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_split_the_initial_vectors():
+    """Two ranks each run half of every round's L initial vectors (the oracle's Alg. 1 round as
+    the per-rank compute); the all-gather selection and the winner's broadcast reproduce the
+    oracle's Alg. 1 on all L vectors: eigenvalues, global tau, components and deflated
+    sketches."""
+    world = 2
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rtpm_rank, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    for r in range(world):
+        lam, tau, dv, ds, lam_ref, tau_ref = res[r]
+        np.testing.assert_allclose(lam, lam_ref, rtol=1e-12)
+        assert tau == tau_ref
+        assert dv < 1e-12 and ds < 1e-10
+    assert res[0][1] == res[1][1]
