@@ -699,7 +699,7 @@ template <typename TIn>
 static int launch_sym_fix(const void* T, int n, int p0, int p1, const int32_t* h, const uint8_t* g,
                           int B, int log2b, void* S, int accumulate, tsk_ctx* ctx) {
   const size_t b = (size_t)1 << log2b;
-  const size_t smax = (size_t)ctx->max_smem_optin - 2048;   // the kernel's static tables
+  const size_t smax = (size_t)ctx->max_smem_optin - 4096;   // the kernel's static tables (2.1 KB)
   auto smem_for = [&](int sk, int lr) {
     return (size_t)sk * 2 * (b >> lr) * sizeof(int) + (size_t)sk * n * sizeof(uint32_t) + 16;
   };
