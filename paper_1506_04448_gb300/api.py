@@ -253,8 +253,8 @@ def robust_power_method_sharded(S: torch.Tensor, h: torch.Tensor, g: torch.Tenso
     of robust_power_method on the device, which also deflates by its own choice in FP64); one
     all-gather of (lambda, global tau) picks the round's winner (select_first_max), and the winner
     broadcasts its component and its deflated sketches, which every rank continues from.  The
-    result equals Alg. 1 on all L vectors.  Returns dict(lam [k] float64, V [k][n], tau [k] int64
-    (global indices), S_deflated).
+    result equals Alg. 1 on all L vectors.  Returns dict(lam [k] float64 and tau [k] int64 (global
+    indices) on the host, V [k][n] and S_deflated on S's device).
 
     run_round(S, U0_round_local [L_local][n], T) -> (lam, tau_local, v [n], S_deflated) may
     replace the device round (the host test of the exchange uses the oracle)."""
@@ -284,7 +284,8 @@ def robust_power_method_sharded(S: torch.Tensor, h: torch.Tensor, g: torch.Tenso
         tau[r] = int(keys[win][1])
         Vs.append(v)
         S = Sd
-    return {"lam": lam, "V": torch.stack(Vs) if Vs else None, "tau": tau, "S_deflated": S}
+    V = torch.stack(Vs) if Vs else U0_local.new_empty((0, U0_local.shape[-1]))
+    return {"lam": lam, "V": V, "tau": tau, "S_deflated": S}
 
 
 def sketch_fft(S: torch.Tensor, inverse: bool = False, out: torch.Tensor | None = None):
