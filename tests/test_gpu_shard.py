@@ -84,6 +84,29 @@ def test_float_planes_match_oracle_and_sum(dev, acc, dtype, tol, n, parts, log2b
         assert rel(Ssum[m].cpu().numpy(), ref) < tol
 
 
+@pytest.mark.parametrize("log2b,B", [(15, 2), (16, 1), (12, 4)])
+def test_planes_int32_input_float_sketch_and_bucket_ranges(dev, log2b, B):
+    """int32 input into complex-float sketches (the fixed-point path), also where the buckets are
+    split into 2 or 4 ranges held by separate blocks (b = 2^15, 2^16) and where one block builds
+    several sketches (b = 2^12, B = 4): each plane range against the oracle's masked sketch, and
+    the sum of the ranges against the full sketch."""
+    n = 40
+    b = 1 << log2b
+    Ti = synth.random_symmetric_int(n, 60 + log2b)
+    h, g = tsk.cs_hashes(3 + log2b, B, log2b, [n], dev)
+    ho, go = O.cs_hashes(3 + log2b, B, log2b, [n])
+    Td = torch.tensor(Ti, device=dev)
+    Ssum = None
+    for p0, p1 in tsk.plane_ranges(n, 3):
+        Sp = tsk.sketch_tensor_planes(Td[p0:p1].contiguous(), h, g, log2b, p0)
+        Tm = np.where(plane_mask(n, p0, p1), Ti, 0).astype(np.float64)
+        for m in range(B):
+            assert rel(Sp[m].cpu().numpy(), O.sketch_tensor_sym(Tm, ho[m, 0], go[m, 0], b)) < 1e-6
+        Ssum = Sp.clone() if Ssum is None else Ssum + Sp
+    full = tsk.sketch_tensor(Td, h, g, log2b).cpu().numpy()
+    assert rel(Ssum.cpu().numpy(), full) < 1e-6
+
+
 def test_planes_accumulate_into_one_buffer(dev):
     """accumulate=True adds each range's part into the same S: after all ranges S is the full
     sketch (here bit-equal to sketch_tensor's int64 result)."""
