@@ -594,6 +594,14 @@ def run_batched(args):
     # same work from a device queue could remove
     busy, n_kernels = gpu_busy_fraction(graph.replay, dev)
     busy_eager, n_eager = gpu_busy_fraction(plan.run, dev)
+    # the same launches enqueued one by one (no graph), timed like the replays: the graph's idle
+    # time between kernels is at most the eager run's
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.run()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    eager_ms = e0.elapsed_time(e1) / args.steps
     work = sum(s["k"] * L * T for s in specs)
     # the same problems, one robust_power_method call after another
     for p in probs[:4]:
@@ -637,6 +645,7 @@ def run_batched(args):
                                  "recovery"},
             "gpu_busy_fraction": {"graph_replay": busy, "graph_kernels": n_kernels,
                                   "eager_run": busy_eager, "eager_kernels": n_eager,
+                                  "eager_run_ms": eager_ms, "graph_replay_ms": t_ms,
                                   "note": "share of the step's span with a kernel running "
                                           "(CUDA activity trace of one untimed call): a single "
                                           "persistent kernel pulling the same work from a device "
