@@ -186,14 +186,13 @@ int contract_iuu(tsk_ctx* ctx, const float* FS, const float* S, const int32_t* h
 
 /* contract_iuu for callers that cannot allocate device memory.  The paper has no counterpart:
  * this is a deployment variant of contract_iuu with the same arguments and result (Vmed only).
- * Callers that run while a stream is being captured into a CUDA graph, or whose device memory
- * belongs to another allocator, cannot let the library cudaMalloc its workspace; this entry
- * point allocates nothing and needs no context.  Its scratch (per-sketch values, per-sketch
+ * Callers whose device memory belongs to another allocator, or whose loops forbid allocation
+ * after start-up, cannot let the library cudaMalloc its workspace; this entry point allocates
+ * nothing and needs no context.  Its scratch (per-sketch values, per-sketch
  * eigenvalue estimates, arrival counters) lives in one static device array of 4 MiB compiled
  * into the library, which every GPU that loads the library holds until the process exits.
  * stream: the cudaStream_t to enqueue on (NULL = legacy default stream); the current device is
- * used.  The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * and should come before any stream capture.  Returns TSK_EUNSUPPORTED when the scratch,
+ * used.  The first call on a device looks up the array's device address (cudaGetSymbolAddress).  Returns TSK_EUNSUPPORTED when the scratch,
  * L*B*n*4 + L*B*4 + L*4 bytes with each part rounded up to 256, would exceed 4 MiB.  All calls
  * share the array: calls whose kernels overlap on the GPU (e.g. on two streams) race.  Having no
  * context, it records no device status: a zero or non-finite input vector is not reported (its

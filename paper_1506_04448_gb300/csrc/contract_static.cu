@@ -2,17 +2,16 @@
 //
 // contract_iuu keeps its per-sketch values, per-sketch eigenvalue estimates and arrival
 // counters in a context workspace that grows with cudaMalloc.  Some callers cannot allocate
-// device memory at the point where they contract: code running while a stream is being
-// captured into a CUDA graph (cudaMalloc is not a stream operation and breaks the capture),
-// runtimes whose device memory is owned by another allocator and may not be touched by a
-// library, and latency-critical loops that forbid allocation after start-up.  This entry point
+// device memory at the point where they contract: runtimes whose device memory is owned by
+// another allocator and may not be touched by a library, and latency-critical loops that
+// forbid allocation after start-up.  This entry point
 // runs the same kernel with that scratch in a fixed-size array compiled into the library
 // (kStaticScratchBytes per device, held by every GPU that loads the library until the process
 // exits) and takes the stream directly, so it creates no context either.
 //
 // The array's host-side name is only a stand-in for a device address, so the address is looked
 // up once per device with cudaGetSymbolAddress, with that device current, the first time the
-// entry point runs there (that first call should therefore come before any stream capture).
+// entry point runs there.
 // All calls share the array and it keeps the last call's contents: the arrival counters are
 // cleared on the stream before every launch, and calls whose kernels overlap on the GPU race.
 #include <mutex>

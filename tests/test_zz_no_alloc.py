@@ -1,7 +1,7 @@
 """contract_iuu_static: the contraction entry point for callers that cannot allocate.
 
-Callers capturing a stream into a CUDA graph, or whose device memory belongs to another
-allocator, cannot let the library cudaMalloc a workspace; contract_iuu_static keeps its scratch
+Callers whose device memory belongs to another allocator, or whose loops forbid allocation
+after start-up, cannot let the library cudaMalloc a workspace; contract_iuu_static keeps its scratch
 in a static device array instead.  This test calls it through the C ABI twice in a row (so the
 second call sees the array as the first one left it) and compares each result with the
 workspace-based contract_iuu within the contraction tolerance (1e-5 relative, 2-norm), and
