@@ -187,25 +187,34 @@ constexpr int kMaxTileCols = 256;   // nc = ceil(n / 32) for n <= 8192
 // rb <= c < nc = ceil(n / 32) and i < min(32 rb + 32, n).  One warp takes one tile: lane l owns
 // column k = 32 c + l (one coalesced 128-byte row segment per row), so the column's hash words
 // stay in registers while the warp walks the tile's rows.  Within a row block rb the tiles are
-// numbered column-major over the planes that reach it.
+// numbered column-major over the planes that reach it.  The fixed-point build and its prepass
+// place the same tiles on indices shifted by (-n) mod 32 (wedge_shift).
 
 // max |T_ijk| over the wedge i <= j <= k as float bits, into *maxbits (zeroed by the caller).
 // Warps take the wedge's tiles (all planes) and load a tile's up to 32 rows at once.
+// Wedge tiles of the fixed-point build are 32 x 32 blocks of (j, k) in the shifted indices
+// j' = j + off, k' = k + off with off = (-n) mod 32, so that the last column block ends exactly at
+// n: a lane never stands beyond the tensor, and the one ragged block (shifted indices below off)
+// is reached only by the planes i < 32 - off.
+__host__ __device__ __forceinline__ int wedge_shift(int n) { return (32 - (n & 31)) & 31; }
+
 template <typename TIn>
 __global__ void __launch_bounds__(256) wedge_absmax_kernel(const TIn* __restrict__ T, int n, int i0,
                                                            int i1, unsigned* maxbits) {
-  // planes [i0, i1): row blocks rb >= i0 / 32, each with planes i0 .. min(i1, 32 rb + 32) - 1
+  // planes [i0, i1) in the shifted indices of wedge_shift: row blocks rb >= (i0 + off) / 32,
+  // each with planes i0 .. min(i1 + off, 32 rb + 32) - off - 1
   __shared__ unsigned smax;
   __shared__ int pre[kMaxTileCols + 1];   // tiles before row block rb0 + q
+  const int off = wedge_shift(n);
   const int nc = (n + 31) >> 5;
-  const int rb0 = i0 >> 5, nrb = nc - rb0;
+  const int rb0 = (i0 + off) >> 5, nrb = nc - rb0;
   if (threadIdx.x == 0) {
     smax = 0u;
     int acc = 0;
     for (int q = 0; q < nrb; ++q) {
       pre[q] = acc;
       const int rb = rb0 + q;
-      acc += max(0, min(i1, 32 * rb + 32) - i0) * (nc - rb);
+      acc += max(0, min(i1 + off, 32 * rb + 32) - (i0 + off)) * (nc - rb);
     }
     pre[nrb] = acc;
   }
@@ -220,14 +229,14 @@ __global__ void __launch_bounds__(256) wedge_absmax_kernel(const TIn* __restrict
       if (pre[mid] <= it) lo = mid; else hi = mid - 1;
     }
     const int rb = rb0 + lo;
-    const int nir = min(i1, 32 * rb + 32) - i0;
+    const int nir = min(i1 + off, 32 * rb + 32) - (i0 + off);
     const int local = it - pre[lo];
     const int c = rb + local / nir;
     const int i = i0 + local % nir;
-    const int jlo = max(i, 32 * rb), jhi = min(32 * rb + 32, n);
-    const int k = 32 * c + lane;
-    const int jlim = k >= n ? -1 : (rb == c ? min(k, jhi - 1) : jhi - 1);
-    const TIn* col = T + ((size_t)i * n + jlo) * n + (k < n ? k : n - 1);
+    const int jlo = max(i, 32 * rb - off), jhi = 32 * rb + 32 - off;
+    const int k = 32 * c + lane - off;
+    const int jlim = rb == c ? min(k, jhi - 1) : jhi - 1;   // no rows for k < 0
+    const TIn* col = T + ((size_t)i * n + jlo) * n + (k < 0 ? 0 : k);
     TIn x[32];
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
@@ -266,7 +275,7 @@ __device__ __forceinline__ FixScale fix_scale(uint32_t mb) {
   return f;
 }
 
-constexpr int kMaxFixSlabs = 256;
+constexpr int kMaxFixParts = 256;
 
 struct SymFixArgs {
   const void* T;
@@ -276,11 +285,11 @@ struct SymFixArgs {
   int B;
   int log2b;
   int log2r;            // 2^log2r bucket ranges, one block each
-  int nslab;
+  int nslab;            // partials per sketch: block s of a sketch takes tiles s, s + nslab, ...
   const unsigned* maxbits;
   int* carry;           // [B][2b]: wraps of the int32 sums past +-2^31
   int* part;            // [nslab][B][2b]: per-block integer partials
-  int plane0[kMaxFixSlabs + 1];   // slab s holds the planes [plane0[s], plane0[s + 1])
+  int p0, p1;           // the planes [p0, p1) are built
 };
 
 // Packed hash word of index i for the fixed-point build: 8 h(i) + g(i) 2^30 (mod 2^32).  In the
@@ -406,50 +415,55 @@ __device__ __forceinline__ void sym_fix_rows_edge(const SymFixArgs& a, const Fix
   }
 }
 
-// The tiles of one block: planes [i0, i1), row blocks rb >= rb0 = i0 / 32, columns c >= rb,
-// planes i < 32 rb + 32 only.  For row block rb there are nir = min(i1, 32 rb + 32) - i0 planes
-// times (nc - rb) columns; pre[] holds the running counts and rcp[] the reciprocals 1 / nir.
-// A warp's items come from the block's counter in increasing order, so its row block only moves
-// forward (a scan from the last one), and local / nir is a float product corrected to the exact
-// quotient (local < 2^24).
+// The tiles of one block, in the shifted indices of wedge_shift: planes [i0, i1), row blocks
+// rb >= rb0 = (i0 + off) / 32, columns c >= rb, planes i + off < 32 rb + 32 only.  For row block
+// rb there are nir = min(i1 + off, 32 rb + 32) - (i0 + off) planes times (nc - rb) columns; pre[]
+// holds the running counts and rcp[] the reciprocals 1 / nir.
+// The block takes every stride-th tile from first on (the blocks of a sketch deal the tiles out
+// round robin, so each gets an even share of every tile size).  A warp's items come from the
+// block's counter in increasing order, so its row block only moves forward (a scan from the last
+// one), and local / nir is a float product corrected to the exact quotient (local < 2^24).
 template <typename TIn, int SK, bool RANGES, bool TWO>
 __device__ __forceinline__ void sym_fix_tiles(const SymFixArgs& a, const FixScale& fs, int* hist,
                                               const uint32_t* qs, const int* pre,
                                               const float* rcp, int nrb, int* next, int i0,
-                                              int i1, int m0, int rr) {
+                                              int i1, int first, int stride, int m0, int rr) {
   const int n = a.n;
-  const int rb0 = i0 >> 5;
+  const int off = wedge_shift(n);
+  const int rb0 = (i0 + off) >> 5;
   const int lane = threadIdx.x & 31;
   const TIn* T = static_cast<const TIn*>(a.T);
   const int items = pre[nrb];
   int lo = 0;   // row block of the warp's last item
   for (;;) {
-    int it = 0;
-    if (lane == 0) it = atomicAdd(next, 1);
-    it = __shfl_sync(0xffffffffu, it, 0);
+    int u = 0;
+    if (lane == 0) u = atomicAdd(next, 1);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    const int it = first + stride * u;   // < items + 32 stride: no int overflow
     if (it >= items) break;
     while (pre[lo + 1] <= it) ++lo;   // row block: last with pre[.] <= it
     const int rb = rb0 + lo;
-    const int nir = min(i1, 32 * rb + 32) - i0;
+    const int nir = min(i1 + off, 32 * rb + 32) - (i0 + off);
     const int local = it - pre[lo];
     int cq = (int)((float)local * rcp[lo]);
     int ir = local - cq * nir;
     if (ir < 0) { --cq; ir += nir; } else if (ir >= nir) { ++cq; ir -= nir; }
     const int c = rb + cq;
     const int i = i0 + ir;
-    const int jlo = max(i, 32 * rb), jhi = min(32 * rb + 32, n);
-    const int k = 32 * c + lane;
+    // rows and column in tensor indices (jhi <= n and k < n, since 32 nc = n + off)
+    const int jlo = max(i, 32 * rb - off), jhi = 32 * rb + 32 - off;
+    const int k = 32 * c + lane - off;
     // last row this lane takes part in: the tile's last row, k itself on the diagonal block
-    // (j <= k), none beyond the tensor
-    const int jlim = k >= n ? -1 : (rb == c ? min(k, jhi - 1) : jhi - 1);
-    // a lane beyond the tensor adds zeros; it takes the word of k mod n, so that its cells are
+    // (j <= k); none for a lane ahead of the tensor (k < 0 <= i, diagonal block only)
+    const int jlim = rb == c ? min(k, jhi - 1) : jhi - 1;
+    // a lane ahead of the tensor adds zeros; it takes the word of k mod n, so that its cells are
     // spread like everyone else's (one shared cell would serialise those adds)
-    int kw = k;   // k mod n (k < n + 32)
-    while (kw >= n) kw -= n;
+    int kw = k;   // k mod n (k >= -31)
+    while (kw < 0) kw += n;
     uint32_t qik[SK];
 #pragma unroll
     for (int s = 0; s < SK; ++s) qik[s] = qs[s * n + i] + qs[s * n + kw];
-    const TIn* col = T + ((size_t)i * n + jlo) * n + (k < n ? k : n - 1);
+    const TIn* col = T + ((size_t)i * n + jlo) * n + (k < 0 ? 0 : k);
     if (rb < c) {
       // off the diagonal block: the plane's first row (j = i, kappa 3) and enough rows after it
       // to leave whole 8-row batches go the per-row path, the batches the interior path
@@ -465,7 +479,7 @@ __device__ __forceinline__ void sym_fix_tiles(const SymFixArgs& a, const FixScal
         sym_fix_rows_edge<TIn, SK, RANGES, TWO>(a, fs, hist, qs, col, i, k, jlo, jmid,
                                                 min(jlim, jmid - 1), qik, m0, rr);
       if (nint > 0)
-        sym_fix_rows_interior<TIn, SK, RANGES, TWO>(a, fs, hist, qs, col + (size_t)e * n, k < n,
+        sym_fix_rows_interior<TIn, SK, RANGES, TWO>(a, fs, hist, qs, col + (size_t)e * n, k >= 0,
                                                     jmid, jmid + nint, qik, m0, rr);
       if (jmid + nint < jhi)
         sym_fix_rows_edge<TIn, SK, RANGES, TWO>(a, fs, hist, qs, col + (size_t)(e + nint) * n, i,
@@ -476,8 +490,8 @@ __device__ __forceinline__ void sym_fix_tiles(const SymFixArgs& a, const FixScal
   }
 }
 
-// Block (group of SK sketches, bucket range rr, slab of planes).  The block's warps take its
-// wedge tiles from a shared counter; per batch of 8 rows a warp has 8 loads in flight per lane,
+// Block (group of SK sketches, bucket range rr, partial s).  The block's warps take its share of
+// the wedge tiles from a shared counter; per batch of 8 rows a warp has 8 loads in flight per lane,
 // scales each entry by kappa 2^(25-E) and, per sketch, flips its sign, rounds it to int32 and
 // adds it to the bucket's re or im cell.
 template <typename TIn, int SK, bool RANGES>
@@ -500,9 +514,10 @@ __global__ void __launch_bounds__(1024, 1) sketch_sym_fix_kernel(SymFixArgs a) {
   const int rr = blockIdx.x % R;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int m0 = grp * SK;
-  const int i0 = a.plane0[blockIdx.y], i1 = a.plane0[blockIdx.y + 1];
+  const int i0 = a.p0, i1 = a.p1;
+  const int off = wedge_shift(n);
   const int nc = (n + 31) >> 5;
-  const int rb0 = i0 >> 5;
+  const int rb0 = (i0 + off) >> 5;
   const int nrb = nc - rb0;
   for (int i = tid; i < SK * cells; i += nt) hist[i] = 0;
   for (int s = 0; s < SK; ++s) {
@@ -515,7 +530,7 @@ __global__ void __launch_bounds__(1024, 1) sketch_sym_fix_kernel(SymFixArgs a) {
     for (int q = 0; q < nrb; ++q) {
       s_pre[q] = acc;
       const int rb = rb0 + q;
-      const int nir = min(i1, 32 * rb + 32) - i0;
+      const int nir = min(i1 + off, 32 * rb + 32) - (i0 + off);
       s_rcp[q] = 1.f / (float)nir;
       acc += nir * (nc - rb);
     }
@@ -523,11 +538,11 @@ __global__ void __launch_bounds__(1024, 1) sketch_sym_fix_kernel(SymFixArgs a) {
   }
   __syncthreads();
   if (fs.sb == 1.f)
-    sym_fix_tiles<TIn, SK, RANGES, false>(a, fs, hist, qs, s_pre, s_rcp, nrb, &s_next, i0, i1, m0,
-                                          rr);
+    sym_fix_tiles<TIn, SK, RANGES, false>(a, fs, hist, qs, s_pre, s_rcp, nrb, &s_next, i0, i1,
+                                          blockIdx.y, a.nslab, m0, rr);
   else
-    sym_fix_tiles<TIn, SK, RANGES, true>(a, fs, hist, qs, s_pre, s_rcp, nrb, &s_next, i0, i1, m0,
-                                         rr);
+    sym_fix_tiles<TIn, SK, RANGES, true>(a, fs, hist, qs, s_pre, s_rcp, nrb, &s_next, i0, i1,
+                                         blockIdx.y, a.nslab, m0, rr);
   __syncthreads();
   for (int s = 0; s < SK; ++s) {
     int* dst = a.part + ((size_t)blockIdx.y * a.B + (m0 + s)) * 2 * b + (size_t)2 * rr * br;
@@ -724,47 +739,19 @@ static int launch_sym_fix(const void* T, int n, int p0, int p1, const int32_t* h
   a.B = B;
   a.log2b = log2b;
   a.log2r = log2r;
-  // one wave of 1024-thread blocks (one per SM); slabs are plane ranges of about equal wedge
-  // size (plane i holds (n - i)(n - i + 1) / 2 entries), none below ~16k entries; only the
-  // planes [p0, p1) are built
+  // one wave of 1024-thread blocks (one per SM): nslab partials per sketch, none with fewer than
+  // ~16k wedge entries; only the planes [p0, p1) are built
   auto tet = [](long long x) { return x * (x + 1) * (x + 2) / 6; };
   const long long W = tet(n - p0) - tet(n - p1);
   long long nslab = (long long)ctx->num_sms / ((long long)groups * R);
   if (nslab < 1) nslab = 1;
   const long long cap = (W + 16383) / 16384;
   if (nslab > cap) nslab = cap;
-  if (nslab > p1 - p0) nslab = p1 - p0;
   if (nslab < 1) nslab = 1;
-  if (nslab > kMaxFixSlabs) nslab = kMaxFixSlabs;
+  if (nslab > kMaxFixParts) nslab = kMaxFixParts;
   a.nslab = (int)nslab;
-  {
-    // slabs of about equal cost: plane i costs its tiles' row batches (rows rounded up to 8)
-    // times their columns, over the row blocks rb >= i / 32 it reaches
-    const int nc = (n + 31) / 32;
-    auto plane_cost = [n, nc](int i) {
-      long long cost = 0;
-      for (int rb = i / 32; rb < nc; ++rb) {
-        const int rows = (rb * 32 + 32 < n ? rb * 32 + 32 : n) - (i > 32 * rb ? i : 32 * rb);
-        cost += (long long)((rows + 7) / 8) * (nc - rb);
-      }
-      return cost;
-    };
-    long long total = 0;
-    for (int i = p0; i < p1; ++i) total += plane_cost(i);
-    a.plane0[0] = p0;
-    int i = p0, s = 1;
-    long long acc = 0;
-    while (s < a.nslab && i < p1) {
-      acc += plane_cost(i++);
-      while (s < a.nslab && acc * a.nslab >= total * s) a.plane0[s++] = i;
-    }
-    while (s < a.nslab) a.plane0[s++] = p1;
-    a.plane0[a.nslab] = p1;
-    for (int q = 1; q < a.nslab; ++q)   // keep every slab non-empty (nslab <= p1 - p0)
-      if (a.plane0[q] <= a.plane0[q - 1]) a.plane0[q] = a.plane0[q - 1] + 1;
-    for (int q = a.nslab - 1; q >= 1; --q)
-      if (a.plane0[q] >= a.plane0[q + 1]) a.plane0[q] = a.plane0[q + 1] - 1;
-  }
+  a.p0 = p0;
+  a.p1 = p1;
   const size_t cells = (size_t)B * 2 * b;
   const size_t head = ws_round(256) + ws_round(cells * sizeof(int));
   int rc = tsk_ws_reserve(ctx, head + ws_round((size_t)a.nslab * cells * sizeof(int)));

@@ -61,7 +61,9 @@ def test_symmetric_int_sketch_bit_exact(dev, n, log2b, B):
 
 
 @pytest.mark.parametrize("n,log2b,B", [(5, 8, 2), (37, 10, 3), (100, 14, 2), (40, 15, 2),
-                                       (40, 16, 3)])
+                                       (40, 16, 3),
+                                       # tile shift (-n) mod 32 of 0, 31 and 15
+                                       (32, 10, 2), (33, 11, 2), (97, 12, 3)])
 def test_symmetric_float_sketch(dev, n, log2b, B):
     b = 1 << log2b
     T = synth.random_symmetric(n, 200 + n)
