@@ -102,6 +102,46 @@ def test_symmetric_sketch_exact_through_int32_wraps(dev, n, log2b, B):
         np.testing.assert_array_equal(S[m], O.sketch_tensor_sym(T, ho[m, 0], go[m, 0], b))
 
 
+def _plant(T, idx, value):
+    i, j, k = idx
+    for a, b_, c in {(i, j, k), (i, k, j), (j, i, k), (j, k, i), (k, i, j), (k, j, i)}:
+        T[a, b_, c] = value
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float64", "int32"])
+def test_symmetric_sketch_max_anywhere_in_a_row(dev, dtype):
+    """The fixed-point scale comes from the prepass's max|T| over the wedge rows T[i][j][j..n-1],
+    read with 16-byte loads between a scalar head and tail.  One entry 1000 times larger than the
+    rest, planted at the start, end or middle of a row (n = 37, so rows start at every offset
+    mod 16 bytes), must set the scale: a missed maximum would overflow its quantised value.
+    Also over a plane range (the prepass reads only the range's planes)."""
+    n, log2b, B = 37, 10, 2
+    b = 1 << log2b
+    h, g = tsk.cs_hashes(71, B, log2b, [n], dev)
+    ho, go = O.cs_hashes(71, B, log2b, [n])
+    for t, idx in enumerate([(0, 0, 0), (0, 0, 36), (0, 1, 2), (5, 9, 9), (5, 9, 36), (12, 20, 29),
+                             (35, 35, 36), (36, 36, 36)]):
+        if dtype == "int32":
+            T = synth.random_symmetric_int(n, 500 + t).astype(np.int64)
+            big = 1000 * int(np.abs(T).max() + 1)
+        else:
+            T = synth.random_symmetric(n, 500 + t)
+            big = 1000.0
+        _plant(T, idx, -big if t % 2 else big)
+        Td = torch.tensor(T, device=dev, dtype=getattr(torch, dtype))
+        Tref = Td.cpu().numpy().astype(np.float64)
+        S = tsk.sketch_tensor(Td, h, g, log2b).cpu().numpy()
+        for m in range(B):
+            assert rel(S[m], O.sketch_tensor_sym(Tref, ho[m, 0], go[m, 0], b)) < 1e-5, (idx, m)
+        p0, p1 = idx[0], min(n, idx[0] + 3)
+        Sp = tsk.sketch_tensor_planes(Td[p0:p1].contiguous(), h, g, log2b, p0).cpu().numpy()
+        mask = np.minimum(np.minimum(np.arange(n)[:, None, None], np.arange(n)[None, :, None]),
+                          np.arange(n)[None, None, :])
+        Tm = np.where((mask >= p0) & (mask < p1), Tref, 0.0)
+        for m in range(B):
+            assert rel(Sp[m], O.sketch_tensor_sym(Tm, ho[m, 0], go[m, 0], b)) < 1e-5, (idx, m)
+
+
 @pytest.mark.parametrize("scale", [1e-30, 1e-3, 1e6, 1e30])
 def test_symmetric_sketch_any_magnitude(dev, scale):
     """The fixed-point step follows max|T| (a power of two), so tiny and huge tensors keep the
