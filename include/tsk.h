@@ -124,8 +124,8 @@ int cs_hashes(tsk_ctx* ctx, uint64_t seed, int B, int log2b, int M, const int64_
  *   rounding is the final conversion to float.  The result does not depend on thread scheduling
  *   (two calls give identical bits).  A non-finite entry (or an FP64 entry beyond the float range)
  *   makes every value of S NaN and is reported by tsk_ctx_status() as TSK_ENONFINITE.  Uses
- *   context workspace of about (nslab + 1) * B * 2b * 4 bytes (M = 1) or (nslab + 1) * B * b * 4
- *   bytes (M = 3), nslab <= the number of SMs.
+ *   context workspace of about (P + 1) * B * 2b * 4 bytes (M = 1) or (P + 1) * B * b * 4 bytes
+ *   (M = 3), where P <= the number of SMs is the number of block partials per sketch.
  * S: [B][b] of acc_dtype.  accumulate = 0 overwrites S, 1 adds to it.
  * Limits: symmetric path log2b <= 16 (M = 1; above 2^14 the buckets are built in 2 or 4
  * ranges by separate blocks), asymmetric path log2b <= 15, n <= 8192. */

@@ -550,9 +550,10 @@ __global__ void __launch_bounds__(1024, 1) sketch_sym_fix_kernel(SymFixArgs a) {
   }
 }
 
-// S[m][c] (+)= 2^(E-25) (sum over slabs of part[.][m][c] + 2^32 carry[m][c]); NaN if max|T| is
-// not finite (also reported as TSK_ENONFINITE).  Four cells per thread with 16-byte loads
-// (cells is a multiple of 4), so that one wave of threads has every slab's loads in flight.
+// S[m][c] (+)= 2^(E-25) (sum over the partials of part[.][m][c] + 2^32 carry[m][c]); NaN if
+// max|T| is not finite (also reported as TSK_ENONFINITE).  Four cells per thread with 16-byte
+// loads (cells is a multiple of 4), so that one wave of threads has every partial's loads in
+// flight.
 __global__ void __launch_bounds__(256) sym_fix_reduce_kernel(const int* __restrict__ part,
                                                              const int* __restrict__ carry,
                                                              const unsigned* maxbits, int nslab,
@@ -719,7 +720,7 @@ static int launch_sym_fix(const void* T, int n, int p0, int p1, const int32_t* h
     return (size_t)sk * 2 * (b >> lr) * sizeof(int) + (size_t)sk * n * sizeof(uint32_t) + 16;
   };
   // fewest bucket ranges whose histogram fits; then the most sketches per block (dividing B,
-  // so every block of a slab does the same work) that still fit
+  // so every block does the same work) that still fit
   int log2r = 0;
   while (smem_for(1, log2r) > smax && log2r < 4) ++log2r;
   if (smem_for(1, log2r) > smax) return TSK_EUNSUPPORTED;

@@ -195,7 +195,7 @@ def test_symmetric_sketch_of_zero_and_nonfinite_tensors(dev):
 @pytest.mark.parametrize("n,log2b,B", [(50, 12, 4), (33, 13, 6), (61, 12, 8)])
 def test_symmetric_float_sketch_several_per_block(dev, n, log2b, B):
     """b <= 2^13 with B divisible by 2 or 4: one block builds two or four sketches from one read
-    of its wedge slab; float and double input."""
+    of its share of the wedge tiles; float and double input."""
     b = 1 << log2b
     T = synth.random_symmetric(n, 300 + n)
     h, g = tsk.cs_hashes(40 + n, B, log2b, [n], dev)
