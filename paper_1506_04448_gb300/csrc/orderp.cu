@@ -122,11 +122,11 @@ __global__ void __launch_bounds__(256) sketch_p_wedge_kernel(const float* T, int
     for (int x = v; x < n; ++x) {
       const float* row = T + (base * n + x) * n;
       const int hx = hp + hs[x], gx = gp + gs[x];
+      // kappa of this row's entries: y == x and y > x
+      const float kdia = fact[p] / (x == v ? denom * fact[run + 2] : denom * fact[run] * 2.f);
+      const float koff = fact[p] / (x == v ? denom * fact[run + 1] : denom * fact[run]);
       for (int y = x + lane; y < n; y += 32) {
-        float dd;
-        if (x == v) dd = (y == x) ? denom * fact[run + 2] : denom * fact[run + 1];
-        else dd = (y == x) ? denom * fact[run] * 2.f : denom * fact[run];
-        const float kappa = fact[p] / dd;
+        const float kappa = y == x ? kdia : koff;
         const float2 val = cscale(root_of_unity(gx + gs[y], mroots), kappa * __ldg(row + y));
         float* slot = reinterpret_cast<float*>(&hist[(hx + hs[y]) & (b - 1)]);
         atomicAdd(slot, val.x);
