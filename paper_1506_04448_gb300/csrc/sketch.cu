@@ -190,14 +190,15 @@ constexpr int kMaxTileCols = 256;   // nc = ceil(n / 32) for n <= 8192
 // numbered column-major over the planes that reach it.  The fixed-point build and its prepass
 // place the same tiles on indices shifted by (-n) mod 32 (wedge_shift).
 
-// max |T_ijk| over the wedge i <= j <= k as float bits, into *maxbits (zeroed by the caller).
-// Warps take the wedge's tiles (all planes) and load a tile's up to 32 rows at once.
 // Wedge tiles of the fixed-point build are 32 x 32 blocks of (j, k) in the shifted indices
 // j' = j + off, k' = k + off with off = (-n) mod 32, so that the last column block ends exactly at
 // n: a lane never stands beyond the tensor, and the one ragged block (shifted indices below off)
 // is reached only by the planes i < 32 - off.
 __host__ __device__ __forceinline__ int wedge_shift(int n) { return (32 - (n & 31)) & 31; }
 
+// max |T_ijk| over the wedge i <= j <= k as float bits, into *maxbits (zeroed by the caller).
+// Warps take the wedge's tiles (all planes, shifted like the build's) and load a tile's up to 32
+// rows at once.
 template <typename TIn>
 __global__ void __launch_bounds__(256) wedge_absmax_kernel(const TIn* __restrict__ T, int n, int i0,
                                                            int i1, unsigned* maxbits) {
